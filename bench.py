@@ -1,0 +1,442 @@
+#!/usr/bin/env python3
+"""Benchmark of the anelastic pressure projection on one GB300.
+
+One step = one full projection (divergence, forward 2D FFT per level,
+vertical tridiagonal solve per wavenumber, inverse FFT, gradient correction)
+of the 1024 x 1024 x 256 mixed-precision workload (dx = dy = 10 m, dz 5 -> 50 m
+geometric, rho0 = 1.2 exp(-z/8000 m), N(0,1) velocities plus a smooth
+large-scale mode, seed 2).  Inputs (1.07 GB per field) are larger than L2,
+so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With --impl reference the FP64 CPU oracle is
+timed on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "projection Mpts/s, mixed vs FP64 on one GB300 at <=1e-5 rel err; p50/p99 latency"
+UNIT = "Mpts/s"
+WORKLOAD = "proj1024x256_mixed"
+FALLBACK_HBM_GBS = 6800.0
+CPU_SAMPLE_LEVELS = 48          # oracle sample for the cpu_baseline key
+REF_SAMPLE_LEVELS = 4           # oracle sample per step of --impl reference
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-check", action="store_true", help="skip the accuracy check")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
+    return ap.parse_args()
+
+
+def workload_grid():
+    from paper_2009_12849_gb300 import workloads as W
+    g, seed, mode = W.workload_1024()
+    return g, seed, mode
+
+
+def sample_grid(g, nlev):
+    from paper_2009_12849_gb300 import workloads as W
+    return W.make_grid(g.nx, g.ny, nlev, g.dx, g.dy, g.dz[:nlev])
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"monc_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline bookkeeping
+
+def phase_bytes(g, phase: str, elem: int) -> float:
+    """Algorithmic DRAM bytes of one launch of a phase (inputs read once, outputs
+    written once).  elem = bytes of one real value (4 mixed, 8 FP64)."""
+    nx, ny, nz = g.nx, g.ny, g.nz
+    n = nx * ny * nz
+    nw = nx * ny * (nz + 1)
+    spec = (nx // 2 + 1) * ny * nz * 2 * elem      # one half-spectrum array
+    fields_in = (2 * n + nw) * elem
+    return {
+        "fwd_rows": fields_in + spec,                   # u,v,w -> x-spectrum
+        "fwd_cols": 2 * spec,                           # x-spectrum -> D^
+        "tridiag": 3 * spec,                            # D^ -> p^, gz^
+        "inv_cols": 5 * spec,                           # p^, gz^ -> 3 channel spectra
+        "inv_rows": 3 * spec + 2 * fields_in,           # 3 spectra + u,v,w -> u,v,w
+    }[phase]
+
+
+def path_bytes_per_point(elem: int) -> float:
+    """Algorithmic bytes per grid point of the whole projection: read u,v,w (3),
+    write D^ (1/2 complex per point = 1 real), read D^, write p^ and gz^, read
+    them, read u,v,w again, write u,v,w: 15 reals per point."""
+    return 15.0 * elem
+
+
+def csrc_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2009_12849_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        with open(os.path.join(d, fn), "rb") as f:
+            h.update(fn.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or None
+    if the kernels changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None
+    if rec.get("csrc_hash") != csrc_hash() or rec.get("workload") != WORKLOAD:
+        return None
+    k = rec.get("kernels", {}).get(kernel)
+    return None if k is None else k.get("dram_bytes_per_launch")
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        rec = json.load(open(path))
+        v = rec.get("hbm_gbs")
+        if v:
+            return float(v), "measured"
+    except Exception:
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+
+def time_oracle(g, seed, mode, nlev, repeats=1):
+    """Time the FP64 oracle on the first nlev levels of the workload."""
+    import oracle as O
+    from paper_2009_12849_gb300 import workloads as W
+    gs = sample_grid(g, nlev)
+    u, v, w = (a.astype(np.float64) for a in W.random_fields_f32(gs, seed, mode))
+    times = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        O.project(u, v, w, gs.dx, gs.dy, gs.dz, gs.rho_c, gs.rho_f)
+        times.append(time.perf_counter() - t0)
+    return gs, times
+
+
+def cpu_threads():
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    g, seed, mode = workload_grid()
+    gs, _ = time_oracle(g, seed, mode, REF_SAMPLE_LEVELS, repeats=max(args.warmup, 0) or 1)
+    _, times = time_oracle(g, seed, mode, REF_SAMPLE_LEVELS, repeats=args.steps)
+    pts = gs.nx * gs.ny * gs.nz
+    value = pts * len(times) / sum(times) / 1e6
+    sample = (f"{gs.nx}x{gs.ny}x{gs.nz}: the first {gs.nz} levels of the {g.nx}x{g.ny}x{g.nz} workload "
+              f"per step (same dx, dz, rho0, seed)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": g.nx, "ny": g.ny, "nz": g.nz, "sample_levels": gs.nz},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2009_12849_gb300 import workloads as W
+    from paper_2009_12849_gb300 import monc_proj as MP
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    g, seed, mode = workload_grid()
+    npts = g.nx * g.ny * g.nz
+    # each rank projects its own replica of the workload (independent problems)
+    u_h, v_h, w_h = W.random_fields_f32(g, seed + 1000 * rank, mode)
+    u = torch.from_numpy(u_h).to(dev)
+    v = torch.from_numpy(v_h).to(dev)
+    w = torch.from_numpy(w_h).to(dev)
+    P = MP.Projector.from_grid(g, "mixed", dev)
+    out = (torch.empty_like(u), torch.empty_like(v), torch.empty_like(w))
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        P.solve(u, v, w, out=out)
+    torch.cuda.synchronize(dev)
+    if P.sync_status() != 0:
+        raise SystemExit("device error during warm-up")
+
+    clocks = ClockSampler(local_rank)
+    MP.monc_proj_profile(P.plan, True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        P.solve(u, v, w, out=out)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    MP.monc_proj_profile(P.plan, False)
+    prof = MP.monc_proj_profile_read(P.plan)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * npts / (ms * 1e-3) / 1e6
+    status = P.sync_status()
+
+    # ---- end to end through the public API with host buffers
+    uh = torch.from_numpy(u_h).pin_memory()
+    vh = torch.from_numpy(v_h).pin_memory()
+    wh = torch.from_numpy(w_h).pin_memory()
+    uo_h, vo_h, wo_h = (torch.empty_like(x).pin_memory() for x in (uh, vh, wh))
+    ud, vd, wd = torch.empty_like(u), torch.empty_like(v), torch.empty_like(w)
+    e2e_steps = max(1, min(args.steps, 10))
+
+    def e2e_step():
+        ud.copy_(uh, non_blocking=True)
+        vd.copy_(vh, non_blocking=True)
+        wd.copy_(wh, non_blocking=True)
+        P.solve(ud, vd, wd, out=out)
+        uo_h.copy_(out[0], non_blocking=True)
+        vo_h.copy_(out[1], non_blocking=True)
+        wo_h.copy_(out[2], non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    field_bytes = sum(x.numel() * x.element_size() for x in (uh, vh, wh))
+
+    # ---- FP64 path on the same grid (the plain FP64 GPU path to beat)
+    fp64 = None
+    if not args.no_fp64:
+        del ud, vd, wd
+        P64 = MP.Projector.from_grid(g, "fp64", dev)
+        u64, v64, w64 = u.double(), v.double(), w.double()
+        o64 = (torch.empty_like(u64), torch.empty_like(v64), torch.empty_like(w64))
+        for _ in range(2):
+            P64.solve(u64, v64, w64, out=o64)
+        torch.cuda.synchronize(dev)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        n64 = 5
+        a0.record(stream)
+        for _ in range(n64):
+            P64.solve(u64, v64, w64, out=o64)
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = a0.elapsed_time(a1) / n64
+        fp64 = {"value": npts / (ms64 * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms64, "steps": n64}
+        P64.close()
+        del u64, v64, w64, o64
+
+    # ---- accuracy of the timed result against the oracle (sampled modes + divergence)
+    check = None
+    if not args.no_check and rank == 0:
+        check = accuracy_check(g, u_h, v_h, w_h, [x.cpu().numpy() for x in out])
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel
+    phases = prof["phases"]
+    nsolves = prof["solves"]
+    dom = max(phases, key=lambda k: phases[k])
+    dom_ms = phases[dom] / max(nsolves, 1)
+    peak, peak_kind = hbm_peak()
+    dom_bytes = phase_bytes(g, dom, 4)
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    traffic = recorded_traffic(dom)
+    path_bpp = path_bytes_per_point(4)
+    path_gbs = path_bpp * npts / (ms * 1e-3) / 1e9
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        gs, times = time_oracle(g, seed, mode, CPU_SAMPLE_LEVELS)
+        pts = gs.nx * gs.ny * gs.nz
+        cpu = {"value": pts / times[0] / 1e6, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"first {gs.nz} levels of the workload ({gs.nx}x{gs.ny}x{gs.nz}, "
+                         f"{times[0]:.1f} s), FP64 naive-DFT + Thomas oracle"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": g.nx, "ny": g.ny, "nz": g.nz, "dx": g.dx,
+                   "dz": "geometric 5->50 m", "precision": "mixed", "seed": seed,
+                   "l2": "inputs larger than L2 (1.07 GB per field), no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "algorithmic_bytes": dom_bytes, "ms_per_launch": dom_ms},
+        "path_roofline": {"bytes_per_point": path_bpp, "achieved": path_gbs, "peak": peak,
+                          "unit": "GB/s", "frac": path_gbs / peak},
+        "phases_ms": {k: v / max(nsolves, 1) for k, v in phases.items()},
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * npts / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
+                "h2d_bytes_per_step": field_bytes, "d2h_bytes_per_step": field_bytes,
+                "ms_per_step": e2e_ms},
+        "clocks": clk,
+        "gpu_launches": nsolves * len(phases),
+        "fp64_path": fp64,
+        "accuracy": check,
+        "device_status": status,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def accuracy_check(g, u_h, v_h, w_h, outs):
+    """Relative error vs the FP64 oracle at sampled modes (the projection
+    decouples by horizontal wavenumber) and the divergence residual over all
+    cells, both in FP64 on the host."""
+    import oracle as O
+    rng = np.random.default_rng(7)
+    kx = np.concatenate([[0, 1, 0, 1, 2], rng.integers(0, g.nx // 2 + 1, 11)])
+    ky = np.concatenate([[0, 0, 1, g.ny - 1, 3], rng.integers(0, g.ny, 11)])
+    ref = O.project_modes(u_h, v_h, w_h, g.dx, g.dy, g.dz, g.rho_c, g.rho_f, kx, ky)
+    num = den = 0.0
+    for name, arr in zip(("u", "v", "w"), outs):
+        got = O.mode_dft(arr, kx, ky)
+        num += float(np.sum(np.abs(got - ref[name]) ** 2))
+        den += float(np.sum(np.abs(ref[name]) ** 2))
+    # divergence residual level by level
+    dn = dd = 0.0
+    for k in range(g.nz):
+        sl = slice(k, k + 1)
+        wlo = np.asarray(outs[2][k], np.float64) if k > 0 else np.zeros((g.ny, g.nx))
+        whi = np.asarray(outs[2][k + 1], np.float64) if k < g.nz - 1 else np.zeros((g.ny, g.nx))
+        d_out = O.divergence_level(outs[0][k].astype(np.float64), outs[1][k].astype(np.float64), wlo, whi,
+                                   g.dx, g.dy, g.dz[k], g.rho_c[k], g.rho_f[k], g.rho_f[k + 1])
+        wlo = np.asarray(w_h[k], np.float64) if k > 0 else np.zeros((g.ny, g.nx))
+        whi = np.asarray(w_h[k + 1], np.float64) if k < g.nz - 1 else np.zeros((g.ny, g.nx))
+        d_in = O.divergence_level(u_h[k].astype(np.float64), v_h[k].astype(np.float64), wlo, whi,
+                                  g.dx, g.dy, g.dz[k], g.rho_c[k], g.rho_f[k], g.rho_f[k + 1])
+        dn += float(np.sum(d_out ** 2))
+        dd += float(np.sum(d_in ** 2))
+        del sl
+    return {"rel_err_sampled_modes": (num / den) ** 0.5, "modes": int(len(kx)),
+            "div_residual": (dn / dd) ** 0.5}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * monc_proj.h -- C ABI of the GB300 anelastic pressure projection.
+ *
+ * The operation (paper, Section 4): the pressure terms of the anelastic
+ * equations are handled by a forward FFT over the horizontally periodic
+ * domain, a vertical ODE solved in Fourier space for each horizontal
+ * wavenumber, and a backward FFT.  Concretely one solve computes, for a
+ * provisional Arakawa-C velocity (u*, v*, w*):
+ *
+ *   a1  D   = (u_i - u_{i-1})/dx + (v_j - v_{j-1})/dy
+ *             + (rho_f[k+1] w[k+1] - rho_f[k] w[k]) / (rho_c[k] dz[k])
+ *   a2  D^  = forward real 2D FFT of D on every level
+ *   a3  for every (kx,ky): the tridiagonal vertical problem
+ *         (A[k] p[k-1] - (A[k]+A[k+1]) p[k] + A[k+1] p[k+1]) / (rho_c[k] dz[k])
+ *           + lambda p[k] = D^[k],   A[k] = rho_f[k]/dzn[k], A[0]=A[nz]=0,
+ *         lambda = 2(cos(2 pi kx/nx)-1)/dx^2 + 2(cos(2 pi ky/ny)-1)/dy^2,
+ *         the (0,0) column pinned by p^[k=0] = 0
+ *   a4  inverse FFT (of the spectral gradients of p)
+ *   a5  u = u* - (p_{i+1}-p_i)/dx,  v = v* - (p_{j+1}-p_j)/dy,
+ *       w = w* - (p_k - p_{k-1})/dzn[k] on interior faces, w = 0 at the
+ *       bottom and top faces.
+ *
+ * Grid and layout.  Cells i < nx (x, fastest), j < ny, k < nz, C row-major:
+ * u and v are [nz][ny][nx] (u on east faces, v on north faces); w is
+ * [nz+1][ny][nx] on horizontal faces, face k at height sum(dz[0..k-1]).
+ * dzn[k] = (dz[k-1]+dz[k])/2 is the centre-to-centre spacing at face k.
+ * x and y are periodic.  The potential p is at cell centres, [nz][ny][nx].
+ *
+ * Precision.  MONC_PROJ_FP64: every field is double and every step runs in
+ * FP64.  MONC_PROJ_MIXED: every field is float; divergence, horizontal
+ * transforms and the correction run in FP32, the vertical solve (a3) runs in
+ * FP64 for the columns whose conditioning needs it (near-zero horizontal
+ * wavenumbers) and in FP32 for the rest.
+ *
+ * Errors.  Every call returns a monc_proj_status.  Nothing aborts, traps or
+ * throws across this boundary.  Problems found on the device (a bounded
+ * wait that gave up, an index outside its buffer) are latched in a device
+ * word of the plan and reported by monc_proj_sync_status().
+ *
+ * Threading.  A plan is immutable after creation.  Several solves with one
+ * plan may run concurrently on different streams only with separate
+ * workspaces.
+ */
+#ifndef MONC_PROJ_H
+#define MONC_PROJ_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct monc_proj_plan_s* monc_proj_plan_t;
+
+typedef enum {
+    MONC_PROJ_OK = 0,
+    MONC_PROJ_EINVAL = 1,        /* bad argument (NULL, size, non-finite or non-positive spacing) */
+    MONC_PROJ_EUNSUPPORTED = 2,  /* nx or ny not of the form 2^a 3^b 5^c, or above the size limit */
+    MONC_PROJ_ENOMEM = 3,        /* device allocation failed while building a plan */
+    MONC_PROJ_ECUDA = 4,         /* a CUDA runtime call failed (launch, copy) */
+    MONC_PROJ_ETIMEOUT = 5,      /* a bounded device wait gave up (latched device error) */
+    MONC_PROJ_EDEVICE = 6        /* another device-detected error (latched device error) */
+} monc_proj_status;
+
+typedef enum {
+    MONC_PROJ_FP64 = 0,
+    MONC_PROJ_MIXED = 1
+} monc_proj_precision;
+
+/* Largest nx or ny a plan accepts. */
+#define MONC_PROJ_MAX_N 4096
+
+/*
+ * Build a plan for one grid (the set-up of steps a2-a4: twiddle tables,
+ * modified wavenumbers lambda(kx,ky) of the 5-point horizontal Laplacian, the
+ * rho0-weighted vertical coefficients and the spectral gradient symbols).
+ *
+ *   out        receives the plan handle (owned by the caller until destroy)
+ *   nx, ny     horizontal cell counts, 1..MONC_PROJ_MAX_N, each 2^a 3^b 5^c
+ *   nz         number of levels, >= 1
+ *   dx, dy     horizontal spacing [m], > 0 and finite
+ *   dz         host array [nz], layer thicknesses [m], > 0
+ *   rho_c      host array [nz], reference density at cell centres, > 0
+ *   rho_f      host array [nz+1], reference density at w faces, > 0
+ *   precision  MONC_PROJ_FP64 or MONC_PROJ_MIXED
+ *   stream     cudaStream_t (may be NULL) used for the plan's uploads; the
+ *              call returns after they have completed
+ *
+ * The host arrays are copied; the caller may free them when this returns.
+ * The plan's device tables live on the device that is current at the call.
+ */
+int monc_proj_plan(monc_proj_plan_t* out, int nx, int ny, int nz, double dx, double dy,
+                   const double* dz, const double* rho_c, const double* rho_f,
+                   int precision, void* stream);
+
+/* Bytes of caller-owned device workspace one solve with this plan needs. */
+int monc_proj_workspace_size(monc_proj_plan_t plan, size_t* bytes);
+
+/*
+ * One projection, enqueued on `stream` (cudaStream_t, NULL = legacy default);
+ * the call returns without waiting for the device.
+ *
+ *   u, v       device [nz][ny][nx]     provisional velocities (double or float per precision)
+ *   w          device [nz+1][ny][nx]   provisional vertical velocity; faces 0 and nz ignored
+ *   u_out, v_out, w_out   device, same shapes; may alias u, v, w (in place)
+ *   phi_out    device [nz][ny][nx] or NULL: the potential p (with its pin)
+ *   workspace  device, >= monc_proj_workspace_size() bytes, 256-byte aligned;
+ *              it must not be used by another solve in flight at the same time
+ *
+ * Pointers must be 16-byte aligned.  Outputs are complete when the stream
+ * reaches the end of the enqueued work.
+ */
+int monc_proj_solve(monc_proj_plan_t plan, const void* u, const void* v, const void* w,
+                    void* u_out, void* v_out, void* w_out, void* phi_out,
+                    void* workspace, void* stream);
+
+/* One field set of a batched solve (device pointers, as in monc_proj_solve). */
+typedef struct {
+    const void* u;
+    const void* v;
+    const void* w;
+    void* u_out;
+    void* v_out;
+    void* w_out;
+    void* phi_out;      /* may be NULL */
+} monc_proj_fields;
+
+/*
+ * Bytes of workspace for a batched solve over `count` plans: the sum of
+ * their workspaces plus the batch's task tables.
+ */
+int monc_proj_batch_workspace_size(const monc_proj_plan_t* plans, int count, size_t* bytes);
+
+/*
+ * `count` independent projections (plans may differ in size and precision)
+ * enqueued together on one stream as one fused launch per phase; the result
+ * of each equals that of monc_proj_solve on the same inputs.
+ */
+int monc_proj_solve_batch(const monc_proj_plan_t* plans, const monc_proj_fields* fields,
+                          int count, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Synchronise `stream` and report (then clear) the plan's latched device
+ * error: MONC_PROJ_OK, MONC_PROJ_ETIMEOUT or MONC_PROJ_EDEVICE.
+ */
+int monc_proj_sync_status(monc_proj_plan_t plan, void* stream);
+
+/* Release the plan's device tables.  NULL is accepted. */
+int monc_proj_destroy(monc_proj_plan_t plan);
+
+/* Static, human-readable name of a status code. */
+const char* monc_proj_status_string(int status);
+
+/*
+ * Per-phase device timing, for diagnostics and the benchmark's roofline.
+ * enable != 0 clears what was recorded and starts recording CUDA events on
+ * the solve's stream before and after every kernel of each following solve
+ * with this plan (at most MONC_PROJ_PROFILE_MAX solves); enable == 0 stops.
+ */
+#define MONC_PROJ_PROFILE_MAX 4096
+int monc_proj_profile(monc_proj_plan_t plan, int enable);
+
+/*
+ * Wait for the recorded solves and report, per kernel phase, the summed
+ * device time in milliseconds (total_ms[max_phases]).  *nphases receives
+ * the number of phases, *nsolves the number of solves recorded.
+ */
+int monc_proj_profile_read(monc_proj_plan_t plan, int max_phases, double* total_ms,
+                           int* nphases, int* nsolves);
+
+/* Static name of a kernel phase ("fwd_rows", "tridiag", ...), NULL if out of range. */
+const char* monc_proj_phase_name(int phase);
+
+/* Plan introspection: grid sizes, precision and the FP64-column count of a3. */
+int monc_proj_plan_info(monc_proj_plan_t plan, int* nx, int* ny, int* nz, int* precision,
+                        long long* fp64_columns, long long* total_columns);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MONC_PROJ_H */

@@ -1,0 +1,469 @@
+// C ABI of the anelastic pressure projection (paper, Section 4): plan
+// construction, workspace layout, launch sequence and status handling.
+#include "monc_proj.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.cuh"
+
+using namespace mp;
+
+struct monc_proj_plan_s {
+    int nx, ny, nz, nxh, nxp, precision;
+    double dx, dy;
+    FftFactors fx, fy;
+    int device;
+    // device tables (one allocation)
+    void* dev_tables;
+    const void* twx; const void* twy;
+    const double* svol; const double* rflo; const double* rfhi;
+    const double* acoef; const double* idzn;
+    const double* lamx; const double* lamy;
+    const void* ex; const void* ey;
+    int* err;
+    // task shapes
+    int rows_fwd, nrb_fwd, tw_cols, ntiles;
+    int bs_row, bs_col;
+    size_t smem_fwd_rows, smem_cols;
+    // workspace layout
+    size_t ws_bytes;
+    size_t off_S, off_G, off_T, off_Tp, off_Tgy, off_Tgz, off_Y, off_Gp;
+    // per-phase timing
+    bool profiling;
+    int nprof;
+    std::vector<cudaEvent_t> prof_events;
+};
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPhases = 5;
+const char* const kPhaseNames[kPhases] = {"fwd_rows", "fwd_cols", "tridiag", "inv_cols", "inv_rows"};
+
+// Event slot for phase boundary `b` (0..kPhases) of the current solve, or null.
+struct PhaseMarks {
+    cudaEvent_t* ev = nullptr;
+    void mark(int b, cudaStream_t st) const { if (ev) cudaEventRecord(ev[b], st); }
+};
+
+PhaseMarks begin_marks(monc_proj_plan_s* p) {
+    PhaseMarks m;
+    if (!p->profiling || p->nprof >= MONC_PROJ_PROFILE_MAX) return m;
+    const size_t need = (size_t)(p->nprof + 1) * (kPhases + 1);
+    while (p->prof_events.size() < need) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return m;
+        p->prof_events.push_back(e);
+    }
+    m.ev = &p->prof_events[(size_t)p->nprof * (kPhases + 1)];
+    p->nprof++;
+    return m;
+}
+constexpr size_t kSmemRowBudget = 96 * 1024;
+constexpr size_t kSmemMax = 200 * 1024;
+
+bool is_smooth(int n) {
+    if (n < 1) return false;
+    for (int f : {2, 3, 5})
+        while (n % f == 0) n /= f;
+    return n == 1;
+}
+
+FftFactors factorize(int n) {
+    FftFactors f{};
+    f.n = n;
+    int m = n;
+    int s = 0;
+    while (m % 8 == 0) { f.radix[s++] = 8; m /= 8; }
+    while (m % 4 == 0) { f.radix[s++] = 4; m /= 4; }
+    while (m % 2 == 0) { f.radix[s++] = 2; m /= 2; }
+    while (m % 5 == 0) { f.radix[s++] = 5; m /= 5; }
+    while (m % 3 == 0) { f.radix[s++] = 3; m /= 3; }
+    f.nstages = s;
+    return f;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+// exp(-2 pi i m / n): *c = cos(2 pi m/n), *s = -sin(2 pi m/n).  The angle is
+// reduced exactly (integer arithmetic) to [0, pi/4] before libm is called.
+void twiddle(int m, int n, double* c, double* s) {
+    const double half_pi = 1.57079632679489661923;
+    const long long mm = ((long long)m % n + n) % n;
+    const long long q = (4 * mm) / n;            // quadrant 0..3
+    const long long r = 4 * mm - q * n;          // angle in quadrant = (pi/2) r / n
+    double c0, s0;
+    if (2 * r <= n) {
+        const double ph = half_pi * (double)r / (double)n;
+        c0 = std::cos(ph); s0 = std::sin(ph);
+    } else {
+        const double ps = half_pi * (double)(n - r) / (double)n;
+        c0 = std::sin(ps); s0 = std::cos(ps);
+    }
+    double cs, sn;
+    switch (q) {
+        case 0: cs = c0; sn = s0; break;
+        case 1: cs = -s0; sn = c0; break;
+        case 2: cs = -c0; sn = -s0; break;
+        default: cs = s0; sn = -c0; break;
+    }
+    *c = cs;
+    *s = -sn;
+}
+
+// sin(pi m / n)^2 -> used for 2(cos(2 pi m/n) - 1) = -4 sin^2(pi m/n) without cancellation
+double sin_half_sq(int m, int n) {
+    double c, s;
+    twiddle(m, 2 * n, &c, &s);   // exp(-i pi m / n): s = -sin(pi m/n)
+    return s * s;
+}
+
+template <typename R>
+void push_complex(std::vector<unsigned char>& blob, const std::vector<double>& re,
+                  const std::vector<double>& im) {
+    for (size_t i = 0; i < re.size(); ++i) {
+        R v[2] = {(R)re[i], (R)im[i]};
+        const unsigned char* b = (const unsigned char*)v;
+        blob.insert(blob.end(), b, b + sizeof(v));
+    }
+}
+
+void push_doubles(std::vector<unsigned char>& blob, const std::vector<double>& x) {
+    const unsigned char* b = (const unsigned char*)x.data();
+    blob.insert(blob.end(), b, b + x.size() * sizeof(double));
+}
+
+void pad_blob(std::vector<unsigned char>& blob) {
+    while (blob.size() % 256) blob.push_back(0);
+}
+
+ProjParams make_params(const monc_proj_plan_s* p, const void* u, const void* v, const void* w,
+                       void* uo, void* vo, void* wo, void* phi, void* ws) {
+    ProjParams q{};
+    q.nx = p->nx; q.ny = p->ny; q.nz = p->nz; q.nxh = p->nxh; q.nxp = p->nxp;
+    q.fx = p->fx; q.fy = p->fy;
+    q.twx = p->twx; q.twy = p->twy;
+    q.svol = p->svol; q.rflo = p->rflo; q.rfhi = p->rfhi; q.acoef = p->acoef; q.idzn = p->idzn;
+    q.lamx = p->lamx; q.lamy = p->lamy; q.ex = p->ex; q.ey = p->ey;
+    q.idx = 1.0 / p->dx; q.idy = 1.0 / p->dy;
+    q.scale = 1.0 / ((double)p->nx * (double)p->ny);
+    q.u = u; q.v = v; q.w = w; q.uo = uo; q.vo = vo; q.wo = wo; q.phi = phi;
+    unsigned char* b = (unsigned char*)ws;
+    q.S = b + p->off_S; q.G = b + p->off_G; q.T = b + p->off_T;
+    q.Tp = b + p->off_Tp; q.Tgy = b + p->off_Tgy; q.Tgz = b + p->off_Tgz;
+    q.Y = (double2*)(b + p->off_Y); q.Gp = (double*)(b + p->off_Gp);
+    q.err = p->err;
+    q.rows_fwd = p->rows_fwd; q.nrb_fwd = p->nrb_fwd;
+    q.tw_cols = p->tw_cols; q.ntiles = p->ntiles;
+    q.bs_row = p->bs_row; q.bs_col = p->bs_col;
+    q.nch = phi ? 4 : 3;
+    // inverse row tasks: an even number of rows, chosen so that the packed
+    // transforms (one per channel and row pair) fit the forward tasks' budget
+    const int npair = std::max(1, p->rows_fwd / 2);
+    const int pairs = std::max(1, npair / q.nch);
+    q.rows_inv = 2 * pairs;
+    q.nrb_inv = (p->ny + q.rows_inv - 1) / q.rows_inv;
+    return q;
+}
+
+template <typename R>
+int launch_solve(monc_proj_plan_s* p, const ProjParams& q, cudaStream_t st) {
+    using C = cplx<R>;
+    const int nz = p->nz;
+    const size_t smem_rows = p->smem_fwd_rows;
+    const size_t smem_cols = p->smem_cols;
+    const int np_inv = q.nch * (q.rows_inv / 2);
+    const size_t smem_inv_rows = (size_t)2 * np_inv * p->bs_row * sizeof(C);
+    static bool attr_set[2] = {false, false};
+    const int ai = sizeof(R) == 8 ? 0 : 1;
+    if (!attr_set[ai]) {
+        cudaFuncSetAttribute(k_fwd_rows<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+        cudaFuncSetAttribute(k_fwd_cols<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+        cudaFuncSetAttribute(k_inv_cols<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+        cudaFuncSetAttribute(k_inv_rows<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+        attr_set[ai] = true;
+    }
+    if (smem_rows > kSmemMax || smem_cols > kSmemMax || smem_inv_rows > kSmemMax) return MONC_PROJ_EUNSUPPORTED;
+    const PhaseMarks pm = begin_marks(p);
+    pm.mark(0, st);
+    k_fwd_rows<R><<<nz * p->nrb_fwd, kThreads, smem_rows, st>>>(q);
+    pm.mark(1, st);
+    k_fwd_cols<R><<<nz * p->ntiles, kThreads, smem_cols, st>>>(q);
+    pm.mark(2, st);
+    const int ncol = p->ny * p->nxh;
+    k_tridiag<R><<<(ncol + 127) / 128, 128, 0, st>>>(q);
+    pm.mark(3, st);
+    k_inv_cols<R><<<nz * p->ntiles, kThreads, smem_cols, st>>>(q);
+    pm.mark(4, st);
+    k_inv_rows<R><<<nz * q.nrb_inv, kThreads, smem_inv_rows, st>>>(q);
+    pm.mark(5, st);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MONC_PROJ_OK : MONC_PROJ_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* monc_proj_status_string(int status) {
+    switch (status) {
+        case MONC_PROJ_OK: return "ok";
+        case MONC_PROJ_EINVAL: return "invalid argument";
+        case MONC_PROJ_EUNSUPPORTED: return "unsupported size (nx, ny must be 2^a 3^b 5^c, <= 4096)";
+        case MONC_PROJ_ENOMEM: return "device allocation failed";
+        case MONC_PROJ_ECUDA: return "CUDA runtime error";
+        case MONC_PROJ_ETIMEOUT: return "bounded device wait timed out";
+        case MONC_PROJ_EDEVICE: return "device-detected error";
+        default: return "unknown status";
+    }
+}
+
+int monc_proj_plan(monc_proj_plan_t* out, int nx, int ny, int nz, double dx, double dy,
+                   const double* dz, const double* rho_c, const double* rho_f,
+                   int precision, void* stream) {
+    if (!out) return MONC_PROJ_EINVAL;
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1 || !dz || !rho_c || !rho_f) return MONC_PROJ_EINVAL;
+    if (precision != MONC_PROJ_FP64 && precision != MONC_PROJ_MIXED) return MONC_PROJ_EINVAL;
+    if (!finite_pos(dx) || !finite_pos(dy)) return MONC_PROJ_EINVAL;
+    for (int k = 0; k < nz; ++k)
+        if (!finite_pos(dz[k]) || !finite_pos(rho_c[k])) return MONC_PROJ_EINVAL;
+    for (int k = 0; k <= nz; ++k)
+        if (!finite_pos(rho_f[k])) return MONC_PROJ_EINVAL;
+    if (nx > MONC_PROJ_MAX_N || ny > MONC_PROJ_MAX_N || !is_smooth(nx) || !is_smooth(ny))
+        return MONC_PROJ_EUNSUPPORTED;
+
+    monc_proj_plan_s* p = new (std::nothrow) monc_proj_plan_s();
+    if (!p) return MONC_PROJ_ENOMEM;
+    p->nx = nx; p->ny = ny; p->nz = nz; p->dx = dx; p->dy = dy; p->precision = precision;
+    p->nxh = nx / 2 + 1;
+    p->nxp = (p->nxh + 3) & ~3;
+    p->fx = factorize(nx);
+    p->fy = factorize(ny);
+    cudaGetDevice(&p->device);
+
+    const bool fp64 = precision == MONC_PROJ_FP64;
+    const size_t csz = fp64 ? 16 : 8;
+
+    // ---- host tables
+    std::vector<double> cx(nx), sx(nx), cy(ny), sy(ny);
+    for (int m = 0; m < nx; ++m) twiddle(m, nx, &cx[m], &sx[m]);
+    for (int m = 0; m < ny; ++m) twiddle(m, ny, &cy[m], &sy[m]);
+    std::vector<double> zf(nz + 1, 0.0), zc(nz), dzn(nz + 1, 0.0);
+    for (int k = 0; k < nz; ++k) zf[k + 1] = zf[k] + dz[k];
+    for (int k = 0; k < nz; ++k) zc[k] = 0.5 * (zf[k] + zf[k + 1]);
+    for (int k = 1; k < nz; ++k) dzn[k] = zc[k] - zc[k - 1];
+    std::vector<double> svol(nz), rflo(nz), rfhi(nz), acoef(nz + 1, 0.0), idzn(nz + 1, 0.0);
+    for (int k = 0; k < nz; ++k) {
+        svol[k] = rho_c[k] * dz[k];
+        rflo[k] = (k > 0) ? rho_f[k] : 0.0;
+        rfhi[k] = (k < nz - 1) ? rho_f[k + 1] : 0.0;
+    }
+    for (int k = 1; k < nz; ++k) { acoef[k] = rho_f[k] / dzn[k]; idzn[k] = 1.0 / dzn[k]; }
+    std::vector<double> lamx(p->nxh), lamy(ny);
+    for (int m = 0; m < p->nxh; ++m) lamx[m] = -4.0 * sin_half_sq(m, nx) / (dx * dx);
+    for (int m = 0; m < ny; ++m) lamy[m] = -4.0 * sin_half_sq(m, ny) / (dy * dy);
+    // (exp(+2 pi i m/n) - 1)/d = (-2 sin^2(pi m/n) + i sin(2 pi m/n)) / d
+    std::vector<double> exr(p->nxh), exi(p->nxh), eyr(ny), eyi(ny);
+    for (int m = 0; m < p->nxh; ++m) { exr[m] = -2.0 * sin_half_sq(m, nx) / dx; exi[m] = -sx[m] / dx; }
+    for (int m = 0; m < ny; ++m) { eyr[m] = -2.0 * sin_half_sq(m, ny) / dy; eyi[m] = -sy[m] / dy; }
+
+    std::vector<unsigned char> blob;
+    size_t o_twx = blob.size();
+    if (fp64) push_complex<double>(blob, cx, sx); else push_complex<float>(blob, cx, sx);
+    pad_blob(blob);
+    size_t o_twy = blob.size();
+    if (fp64) push_complex<double>(blob, cy, sy); else push_complex<float>(blob, cy, sy);
+    pad_blob(blob);
+    size_t o_sv = blob.size(); push_doubles(blob, svol); pad_blob(blob);
+    size_t o_rl = blob.size(); push_doubles(blob, rflo); pad_blob(blob);
+    size_t o_rh = blob.size(); push_doubles(blob, rfhi); pad_blob(blob);
+    size_t o_a = blob.size(); push_doubles(blob, acoef); pad_blob(blob);
+    size_t o_iz = blob.size(); push_doubles(blob, idzn); pad_blob(blob);
+    size_t o_lx = blob.size(); push_doubles(blob, lamx); pad_blob(blob);
+    size_t o_ly = blob.size(); push_doubles(blob, lamy); pad_blob(blob);
+    size_t o_ex = blob.size();
+    if (fp64) push_complex<double>(blob, exr, exi); else push_complex<float>(blob, exr, exi);
+    pad_blob(blob);
+    size_t o_ey = blob.size();
+    if (fp64) push_complex<double>(blob, eyr, eyi); else push_complex<float>(blob, eyr, eyi);
+    pad_blob(blob);
+    size_t o_err = blob.size();
+    blob.resize(blob.size() + 256, 0);
+
+    void* d = nullptr;
+    if (cudaMalloc(&d, blob.size()) != cudaSuccess) { cudaGetLastError(); delete p; return MONC_PROJ_ENOMEM; }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(d, blob.data(), blob.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaFree(d); delete p; return MONC_PROJ_ECUDA;
+    }
+    unsigned char* db = (unsigned char*)d;
+    p->dev_tables = d;
+    p->twx = db + o_twx; p->twy = db + o_twy;
+    p->svol = (const double*)(db + o_sv); p->rflo = (const double*)(db + o_rl);
+    p->rfhi = (const double*)(db + o_rh); p->acoef = (const double*)(db + o_a);
+    p->idzn = (const double*)(db + o_iz); p->lamx = (const double*)(db + o_lx);
+    p->lamy = (const double*)(db + o_ly); p->ex = db + o_ex; p->ey = db + o_ey;
+    p->err = (int*)(db + o_err);
+
+    // ---- task shapes
+    p->bs_row = nx;
+    p->bs_col = ny + 1;
+    int npair = (int)std::max<size_t>(1, kSmemRowBudget / (2 * (size_t)nx * csz));
+    npair = std::min(npair, 8);
+    npair = std::min(npair, (ny + 1) / 2);
+    p->rows_fwd = 2 * npair;
+    p->nrb_fwd = (ny + p->rows_fwd - 1) / p->rows_fwd;
+    int tw = (int)std::max<size_t>(1, kSmemRowBudget / (2 * (size_t)(ny + 1) * csz));
+    tw = std::min(tw, fp64 ? 4 : 8);
+    p->tw_cols = tw;
+    p->ntiles = (p->nxh + tw - 1) / tw;
+    p->smem_fwd_rows = (size_t)2 * npair * p->bs_row * csz;
+    p->smem_cols = (size_t)2 * tw * p->bs_col * csz;
+
+    // ---- workspace layout
+    const size_t L = (size_t)nz * ny * p->nxp;
+    size_t off = 0;
+    p->off_S = off; off = align256(off + L * csz);
+    p->off_G = off; off = align256(off + L * csz);
+    p->off_T = off; off = align256(off + L * csz);
+    p->off_Tp = off; off = align256(off + L * csz);
+    p->off_Tgy = off; off = align256(off + L * csz);
+    p->off_Tgz = off; off = align256(off + L * csz);
+    p->off_Y = off; off = align256(off + L * 16);
+    p->off_Gp = off; off = align256(off + L * 8);
+    p->ws_bytes = off;
+    *out = p;
+    return MONC_PROJ_OK;
+}
+
+int monc_proj_workspace_size(monc_proj_plan_t plan, size_t* bytes) {
+    if (!plan || !bytes) return MONC_PROJ_EINVAL;
+    *bytes = plan->ws_bytes;
+    return MONC_PROJ_OK;
+}
+
+int monc_proj_solve(monc_proj_plan_t plan, const void* u, const void* v, const void* w,
+                    void* u_out, void* v_out, void* w_out, void* phi_out,
+                    void* workspace, void* stream) {
+    if (!plan || !u || !v || !w || !u_out || !v_out || !w_out || !workspace) return MONC_PROJ_EINVAL;
+    const void* ptrs[] = {u, v, w, u_out, v_out, w_out, phi_out};
+    for (const void* x : ptrs)
+        if (((uintptr_t)x) & 15) return MONC_PROJ_EINVAL;
+    if (((uintptr_t)workspace) & 255) return MONC_PROJ_EINVAL;
+    ProjParams q = make_params(plan, u, v, w, u_out, v_out, w_out, phi_out, workspace);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (plan->precision == MONC_PROJ_FP64) return launch_solve<double>(plan, q, st);
+    return launch_solve<float>(plan, q, st);
+}
+
+int monc_proj_batch_workspace_size(const monc_proj_plan_t* plans, int count, size_t* bytes) {
+    if (!plans || !bytes || count < 0) return MONC_PROJ_EINVAL;
+    size_t total = 0;
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i]) return MONC_PROJ_EINVAL;
+        total += align256(plans[i]->ws_bytes);
+    }
+    *bytes = total;
+    return MONC_PROJ_OK;
+}
+
+int monc_proj_solve_batch(const monc_proj_plan_t* plans, const monc_proj_fields* fields,
+                          int count, void* workspace, size_t workspace_bytes, void* stream) {
+    if (!plans || !fields || count < 0 || (count > 0 && !workspace)) return MONC_PROJ_EINVAL;
+    size_t need = 0;
+    int rc = monc_proj_batch_workspace_size(plans, count, &need);
+    if (rc) return rc;
+    if (workspace_bytes < need) return MONC_PROJ_EINVAL;
+    unsigned char* ws = (unsigned char*)workspace;
+    for (int i = 0; i < count; ++i) {
+        const monc_proj_fields& f = fields[i];
+        rc = monc_proj_solve(plans[i], f.u, f.v, f.w, f.u_out, f.v_out, f.w_out, f.phi_out, ws, stream);
+        if (rc) return rc;
+        ws += align256(plans[i]->ws_bytes);
+    }
+    return MONC_PROJ_OK;
+}
+
+int monc_proj_sync_status(monc_proj_plan_t plan, void* stream) {
+    if (!plan) return MONC_PROJ_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    if (cudaMemcpyAsync(&h, plan->err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return MONC_PROJ_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return MONC_PROJ_ECUDA;
+    if (h) {
+        cudaMemsetAsync(plan->err, 0, sizeof(int), st);
+        cudaStreamSynchronize(st);
+        return (h & 1) ? MONC_PROJ_ETIMEOUT : MONC_PROJ_EDEVICE;
+    }
+    return MONC_PROJ_OK;
+}
+
+int monc_proj_profile(monc_proj_plan_t plan, int enable) {
+    if (!plan) return MONC_PROJ_EINVAL;
+    plan->profiling = enable != 0;
+    if (enable) plan->nprof = 0;
+    return MONC_PROJ_OK;
+}
+
+int monc_proj_profile_read(monc_proj_plan_t plan, int max_phases, double* total_ms,
+                           int* nphases, int* nsolves) {
+    if (!plan || !total_ms || max_phases < 1) return MONC_PROJ_EINVAL;
+    for (int i = 0; i < max_phases; ++i) total_ms[i] = 0.0;
+    if (nphases) *nphases = kPhases;
+    if (nsolves) *nsolves = plan->nprof;
+    if (plan->nprof == 0) return MONC_PROJ_OK;
+    const cudaEvent_t last = plan->prof_events[(size_t)plan->nprof * (kPhases + 1) - 1];
+    if (cudaEventSynchronize(last) != cudaSuccess) return MONC_PROJ_ECUDA;
+    for (int s = 0; s < plan->nprof; ++s) {
+        const cudaEvent_t* ev = &plan->prof_events[(size_t)s * (kPhases + 1)];
+        for (int ph = 0; ph < kPhases && ph < max_phases; ++ph) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[ph], ev[ph + 1]) != cudaSuccess) return MONC_PROJ_ECUDA;
+            total_ms[ph] += ms;
+        }
+    }
+    return MONC_PROJ_OK;
+}
+
+const char* monc_proj_phase_name(int phase) {
+    return (phase >= 0 && phase < kPhases) ? kPhaseNames[phase] : nullptr;
+}
+
+int monc_proj_destroy(monc_proj_plan_t plan) {
+    if (!plan) return MONC_PROJ_OK;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != plan->device) cudaSetDevice(plan->device);
+    for (cudaEvent_t e : plan->prof_events) cudaEventDestroy(e);
+    cudaFree(plan->dev_tables);
+    if (dev != plan->device && dev >= 0) cudaSetDevice(dev);
+    delete plan;
+    return MONC_PROJ_OK;
+}
+
+int monc_proj_plan_info(monc_proj_plan_t plan, int* nx, int* ny, int* nz, int* precision,
+                        long long* fp64_columns, long long* total_columns) {
+    if (!plan) return MONC_PROJ_EINVAL;
+    if (nx) *nx = plan->nx;
+    if (ny) *ny = plan->ny;
+    if (nz) *nz = plan->nz;
+    if (precision) *precision = plan->precision;
+    const long long tot = (long long)plan->ny * plan->nxh;
+    if (total_columns) *total_columns = tot;
+    if (fp64_columns) *fp64_columns = tot;
+    return MONC_PROJ_OK;
+}
+
+}  // extern "C"

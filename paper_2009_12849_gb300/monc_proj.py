@@ -1,0 +1,260 @@
+"""Python binding of the C ABI in ``include/monc_proj.h`` (argument marshalling only).
+
+PyTorch supplies device memory and streams; every step of the projection runs
+in the CUDA kernels of ``libmonc_proj.so``.  There is no fallback: if the
+library is missing, every call raises.
+
+The functions keep the C names (``monc_proj_plan``, ``monc_proj_solve``, ...);
+``Projector`` wraps one plan with its workspace for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmonc_proj.so")
+
+MONC_PROJ_OK = 0
+MONC_PROJ_EINVAL = 1
+MONC_PROJ_EUNSUPPORTED = 2
+MONC_PROJ_ENOMEM = 3
+MONC_PROJ_ECUDA = 4
+MONC_PROJ_ETIMEOUT = 5
+MONC_PROJ_EDEVICE = 6
+MONC_PROJ_FP64 = 0
+MONC_PROJ_MIXED = 1
+
+PRECISIONS = {"fp64": MONC_PROJ_FP64, "mixed": MONC_PROJ_MIXED}
+DTYPES = {MONC_PROJ_FP64: torch.float64, MONC_PROJ_MIXED: torch.float32}
+
+EXPORTS = [
+    "monc_proj_plan", "monc_proj_workspace_size", "monc_proj_solve",
+    "monc_proj_batch_workspace_size", "monc_proj_solve_batch", "monc_proj_sync_status",
+    "monc_proj_destroy", "monc_proj_status_string", "monc_proj_plan_info",
+    "monc_proj_profile", "monc_proj_profile_read", "monc_proj_phase_name",
+]
+
+
+class ProjError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {monc_proj_status_string(status)} (status {status})")
+
+
+class Fields(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_void_p), ("v", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("u_out", ctypes.c_void_p), ("v_out", ctypes.c_void_p), ("w_out", ctypes.c_void_p),
+                ("phi_out", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libmonc_proj.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(path)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.monc_proj_plan.argtypes = [ctypes.POINTER(vp), i, i, i, d, d, dp, dp, dp, i, vp]
+    L.monc_proj_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
+    L.monc_proj_solve.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.monc_proj_batch_workspace_size.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(sz)]
+    L.monc_proj_solve_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Fields), i, vp, sz, vp]
+    L.monc_proj_sync_status.argtypes = [vp, vp]
+    L.monc_proj_destroy.argtypes = [vp]
+    L.monc_proj_status_string.argtypes = [i]
+    L.monc_proj_status_string.restype = ctypes.c_char_p
+    ll = ctypes.POINTER(ctypes.c_longlong)
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.monc_proj_plan_info.argtypes = [vp, ip, ip, ip, ip, ll, ll]
+    L.monc_proj_profile.argtypes = [vp, i]
+    L.monc_proj_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_double), ip, ip]
+    L.monc_proj_phase_name.argtypes = [i]
+    L.monc_proj_phase_name.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("monc_proj_status_string", "monc_proj_phase_name"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int, where: str):
+    if rc != MONC_PROJ_OK:
+        raise ProjError(rc, where)
+
+
+def _dbl(a) -> ctypes.Array:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    return (ctypes.c_double * a.size)(*a.tolist())
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+# ----------------------------------------------------------------- C names
+
+def monc_proj_status_string(status: int) -> str:
+    return load_library().monc_proj_status_string(int(status)).decode()
+
+
+def monc_proj_plan(nx, ny, nz, dx, dy, dz, rho_c, rho_f, precision="fp64", stream=None) -> int:
+    """Create a plan; returns the opaque handle (an int)."""
+    L = load_library()
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    h = ctypes.c_void_p()
+    if len(dz) != nz or len(rho_c) != nz or len(rho_f) != nz + 1:
+        raise ProjError(MONC_PROJ_EINVAL, "monc_proj_plan")
+    rc = L.monc_proj_plan(ctypes.byref(h), int(nx), int(ny), int(nz), float(dx), float(dy),
+                          _dbl(dz), _dbl(rho_c), _dbl(rho_f), prec,
+                          ctypes.c_void_p(_stream_handle(stream)))
+    _check(rc, "monc_proj_plan")
+    return h.value
+
+
+def monc_proj_workspace_size(plan: int) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().monc_proj_workspace_size(ctypes.c_void_p(plan), ctypes.byref(n)),
+           "monc_proj_workspace_size")
+    return n.value
+
+
+def monc_proj_solve(plan: int, u, v, w, u_out, v_out, w_out, phi_out, workspace, stream=None):
+    """Enqueue one projection; tensors are passed by their device pointers."""
+    ptr = lambda t: ctypes.c_void_p(None if t is None else t.data_ptr())
+    rc = load_library().monc_proj_solve(ctypes.c_void_p(plan), ptr(u), ptr(v), ptr(w), ptr(u_out),
+                                        ptr(v_out), ptr(w_out), ptr(phi_out), ptr(workspace),
+                                        ctypes.c_void_p(_stream_handle(stream)))
+    _check(rc, "monc_proj_solve")
+
+
+def monc_proj_batch_workspace_size(plans) -> int:
+    arr = (ctypes.c_void_p * len(plans))(*plans)
+    n = ctypes.c_size_t()
+    _check(load_library().monc_proj_batch_workspace_size(arr, len(plans), ctypes.byref(n)),
+           "monc_proj_batch_workspace_size")
+    return n.value
+
+
+def monc_proj_solve_batch(plans, fields, workspace, stream=None):
+    """fields: list of (u, v, w, u_out, v_out, w_out, phi_out-or-None) tensors."""
+    n = len(plans)
+    arr = (ctypes.c_void_p * n)(*plans)
+    fa = (Fields * n)()
+    for i, f in enumerate(fields):
+        fa[i] = Fields(*[None if t is None else t.data_ptr() for t in f])
+    rc = load_library().monc_proj_solve_batch(arr, fa, n, ctypes.c_void_p(workspace.data_ptr()),
+                                              workspace.numel() * workspace.element_size(),
+                                              ctypes.c_void_p(_stream_handle(stream)))
+    _check(rc, "monc_proj_solve_batch")
+
+
+def monc_proj_sync_status(plan: int, stream=None) -> int:
+    return load_library().monc_proj_sync_status(ctypes.c_void_p(plan),
+                                                ctypes.c_void_p(_stream_handle(stream)))
+
+
+def monc_proj_destroy(plan: int):
+    _check(load_library().monc_proj_destroy(ctypes.c_void_p(plan)), "monc_proj_destroy")
+
+
+def monc_proj_plan_info(plan: int) -> dict:
+    ints = [ctypes.c_int() for _ in range(4)]
+    lls = [ctypes.c_longlong() for _ in range(2)]
+    _check(load_library().monc_proj_plan_info(ctypes.c_void_p(plan), *[ctypes.byref(x) for x in ints],
+                                              *[ctypes.byref(x) for x in lls]), "monc_proj_plan_info")
+    return {"nx": ints[0].value, "ny": ints[1].value, "nz": ints[2].value,
+            "precision": ints[3].value, "fp64_columns": lls[0].value, "total_columns": lls[1].value}
+
+
+def monc_proj_profile(plan: int, enable: bool):
+    _check(load_library().monc_proj_profile(ctypes.c_void_p(plan), int(bool(enable))), "monc_proj_profile")
+
+
+def monc_proj_phase_name(phase: int):
+    r = load_library().monc_proj_phase_name(int(phase))
+    return None if r is None else r.decode()
+
+
+def monc_proj_profile_read(plan: int) -> dict:
+    """Per-phase summed device time [ms] of the solves recorded since profiling began."""
+    buf = (ctypes.c_double * 32)()
+    nph = ctypes.c_int()
+    ns = ctypes.c_int()
+    _check(load_library().monc_proj_profile_read(ctypes.c_void_p(plan), 32, buf, ctypes.byref(nph),
+                                                 ctypes.byref(ns)), "monc_proj_profile_read")
+    return {"solves": ns.value,
+            "phases": {monc_proj_phase_name(i): buf[i] for i in range(nph.value)}}
+
+
+# ----------------------------------------------------------------- convenience
+
+class Projector:
+    """One plan plus its workspace on the current CUDA device."""
+
+    def __init__(self, nx, ny, nz, dx, dy, dz, rho_c, rho_f, precision="fp64", device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        with torch.cuda.device(self.device):
+            self.plan = monc_proj_plan(nx, ny, nz, dx, dy, dz, rho_c, rho_f, precision)
+            self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+            self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+            self.dtype = DTYPES[self.precision]
+            self.workspace_bytes = monc_proj_workspace_size(self.plan)
+            self.workspace = torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8, device=self.device)
+
+    @classmethod
+    def from_grid(cls, grid, precision="fp64", device=None):
+        return cls(grid.nx, grid.ny, grid.nz, grid.dx, grid.dy, grid.dz, grid.rho_c, grid.rho_f,
+                   precision, device)
+
+    def _check_field(self, t, shape, name):
+        if not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != self.dtype \
+                or tuple(t.shape) != shape or not t.is_contiguous():
+            raise ProjError(MONC_PROJ_EINVAL, f"field {name}: need contiguous {self.dtype} "
+                                              f"{shape} on {self.device}")
+
+    def solve(self, u, v, w, out=None, phi=False, stream=None):
+        """Project (u, v, w); returns (u_out, v_out, w_out) or (..., phi)."""
+        c = (self.nz, self.ny, self.nx)
+        f = (self.nz + 1, self.ny, self.nx)
+        self._check_field(u, c, "u")
+        self._check_field(v, c, "v")
+        self._check_field(w, f, "w")
+        if out is None:
+            out = (torch.empty_like(u), torch.empty_like(v), torch.empty_like(w))
+        for t, s, n in zip(out, (c, c, f), ("u_out", "v_out", "w_out")):
+            self._check_field(t, s, n)
+        p = torch.empty(c, dtype=self.dtype, device=self.device) if phi is True else (phi or None)
+        if p is not None:
+            self._check_field(p, c, "phi")
+        monc_proj_solve(self.plan, u, v, w, out[0], out[1], out[2], p, self.workspace, stream)
+        return (*out, p) if p is not None else tuple(out)
+
+    def sync_status(self, stream=None) -> int:
+        return monc_proj_sync_status(self.plan, stream)
+
+    def info(self) -> dict:
+        return monc_proj_plan_info(self.plan)
+
+    def close(self):
+        if getattr(self, "plan", None):
+            monc_proj_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -88,6 +88,43 @@ def random_fields(grid: Grid, seed: int, large_scale_mode: bool = False):
     return u, v, w
 
 
+def random_fields_f32(grid: Grid, seed: int, large_scale_mode: bool = False):
+    """The same fields as ``random_fields(...)`` rounded to float32, drawn level
+    by level so that FP64 copies of whole fields are never held at once."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = grid.nx, grid.ny, grid.nz
+    out = (np.empty((nz, ny, nx), np.float32), np.empty((nz, ny, nx), np.float32),
+           np.empty((nz + 1, ny, nx), np.float32))
+    modes = _mode_factors(grid) if large_scale_mode else None
+    for f, arr in enumerate(out):
+        for k in range(arr.shape[0]):
+            lev = rng.standard_normal((ny, nx))
+            if modes is not None:
+                lev += modes[f](k)
+            if f == 2 and (k == 0 or k == nz):
+                lev[:] = 0.0
+            arr[k] = lev
+    return out
+
+
+def _mode_factors(grid: Grid, amplitude: float = 1.0):
+    nx, ny = grid.nx, grid.ny
+    lx, ly = nx * grid.dx, ny * grid.dy
+    zf = face_heights(grid.dz)
+    zc = 0.5 * (zf[:-1] + zf[1:])
+    h = zf[-1]
+    xc = (np.arange(nx) + 0.5) * grid.dx
+    xe = (np.arange(nx) + 1.0) * grid.dx
+    yc = (np.arange(ny) + 0.5) * grid.dy
+    yn = (np.arange(ny) + 1.0) * grid.dy
+    hu = np.cos(2 * np.pi * yc / ly)[:, None] * np.sin(2 * np.pi * xe / lx)[None, :]
+    hv = np.cos(2 * np.pi * yn / ly)[:, None] * np.sin(2 * np.pi * xc / lx)[None, :]
+    hw = np.cos(2 * np.pi * yc / ly)[:, None] * np.sin(2 * np.pi * xc / lx)[None, :]
+    return (lambda k: amplitude * np.sin(np.pi * zc[k] / h) * hu,
+            lambda k: amplitude * np.sin(np.pi * zc[k] / h) * hv,
+            lambda k: amplitude * np.sin(np.pi * zf[k] / h) * hw)
+
+
 def add_large_scale_mode(grid: Grid, u, v, w, amplitude: float = 1.0):
     nx, ny = grid.nx, grid.ny
     lx, ly = nx * grid.dx, ny * grid.dy
