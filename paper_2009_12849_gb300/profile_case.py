@@ -1,0 +1,45 @@
+"""Run a few projections of one synthetic grid, for profiling under ncu.
+
+    python -m paper_2009_12849_gb300.profile_case --grid 512,512,64 --precision mixed --solves 3
+
+Inputs are the seeded workload recipe (N(0,1) plus the large-scale mode,
+dx = dy = 10 m, dz geometric 5 -> 50 m).  Prints the wall time per solve.
+"""
+from __future__ import annotations
+
+import argparse
+import time
+
+import torch
+
+from paper_2009_12849_gb300 import monc_proj as MP
+from paper_2009_12849_gb300 import workloads as W
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--grid", default="512,512,64")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--solves", type=int, default=3)
+    a = ap.parse_args()
+    nx, ny, nz = (int(x) for x in a.grid.split(","))
+    g = W.make_grid(nx, ny, nz, 10.0, 10.0, W.geometric_dz(nz, 5.0, 50.0))
+    dt = torch.float32 if a.precision == "mixed" else torch.float64
+    dev = torch.device("cuda", 0)
+    u, v, w = (torch.from_numpy(x).to(dev, dt) for x in W.random_fields_f32(g, 2, True))
+    P = MP.Projector.from_grid(g, a.precision, dev)
+    out = (torch.empty_like(u), torch.empty_like(v), torch.empty_like(w))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.solves):
+        P.solve(u, v, w, out=out)
+    torch.cuda.synchronize()
+    dt_s = (time.perf_counter() - t0) / a.solves
+    st = P.sync_status()
+    print(f"{nx}x{ny}x{nz} {a.precision}: {dt_s * 1e3:.3f} ms/solve (wall), status {st}")
+    if st != 0:
+        raise SystemExit(1)
+
+
+if __name__ == "__main__":
+    main()
