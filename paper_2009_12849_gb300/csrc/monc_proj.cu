@@ -210,28 +210,9 @@ int launch_solve(monc_proj_plan_s* p, const ProjParams& q, cudaStream_t st) {
     return e == cudaSuccess ? MONC_PROJ_OK : MONC_PROJ_ECUDA;
 }
 
-}  // namespace
-
-extern "C" {
-
-const char* monc_proj_status_string(int status) {
-    switch (status) {
-        case MONC_PROJ_OK: return "ok";
-        case MONC_PROJ_EINVAL: return "invalid argument";
-        case MONC_PROJ_EUNSUPPORTED: return "unsupported size (nx, ny must be 2^a 3^b 5^c, <= 4096)";
-        case MONC_PROJ_ENOMEM: return "device allocation failed";
-        case MONC_PROJ_ECUDA: return "CUDA runtime error";
-        case MONC_PROJ_ETIMEOUT: return "bounded device wait timed out";
-        case MONC_PROJ_EDEVICE: return "device-detected error";
-        default: return "unknown status";
-    }
-}
-
-int monc_proj_plan(monc_proj_plan_t* out, int nx, int ny, int nz, double dx, double dy,
-                   const double* dz, const double* rho_c, const double* rho_f,
-                   int precision, void* stream) {
-    if (!out) return MONC_PROJ_EINVAL;
-    *out = nullptr;
+// Argument checks shared by every entry point that takes grid arguments.
+int validate_grid(int nx, int ny, int nz, double dx, double dy, const double* dz,
+                  const double* rho_c, const double* rho_f, int precision) {
     if (nx < 1 || ny < 1 || nz < 1 || !dz || !rho_c || !rho_f) return MONC_PROJ_EINVAL;
     if (precision != MONC_PROJ_FP64 && precision != MONC_PROJ_MIXED) return MONC_PROJ_EINVAL;
     if (!finite_pos(dx) || !finite_pos(dy)) return MONC_PROJ_EINVAL;
@@ -242,14 +223,24 @@ int monc_proj_plan(monc_proj_plan_t* out, int nx, int ny, int nz, double dx, dou
     if (nx > MONC_PROJ_MAX_N || ny > MONC_PROJ_MAX_N || !is_smooth(nx) || !is_smooth(ny))
         return MONC_PROJ_EUNSUPPORTED;
 
-    monc_proj_plan_s* p = new (std::nothrow) monc_proj_plan_s();
-    if (!p) return MONC_PROJ_ENOMEM;
+    return MONC_PROJ_OK;
+}
+
+// Offsets of the plan's device tables inside one contiguous blob.
+struct TableOffsets {
+    size_t twx, twy, sv, rl, rh, a, iz, lx, ly, ex, ey, err;
+};
+
+// Fill the host-side part of a plan (sizes, radix plans, task shapes,
+// workspace layout) and build its device tables in `blob` (host memory).
+void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double dy,
+                  const double* dz, const double* rho_c, const double* rho_f, int precision,
+                  std::vector<unsigned char>& blob, TableOffsets& to) {
     p->nx = nx; p->ny = ny; p->nz = nz; p->dx = dx; p->dy = dy; p->precision = precision;
     p->nxh = nx / 2 + 1;
     p->nxp = (p->nxh + 3) & ~3;
     p->fx = factorize(nx);
     p->fy = factorize(ny);
-    cudaGetDevice(&p->device);
 
     const bool fp64 = precision == MONC_PROJ_FP64;
     const size_t csz = fp64 ? 16 : 8;
@@ -277,44 +268,27 @@ int monc_proj_plan(monc_proj_plan_t* out, int nx, int ny, int nz, double dx, dou
     for (int m = 0; m < p->nxh; ++m) { exr[m] = -2.0 * sin_half_sq(m, nx) / dx; exi[m] = -sx[m] / dx; }
     for (int m = 0; m < ny; ++m) { eyr[m] = -2.0 * sin_half_sq(m, ny) / dy; eyi[m] = -sy[m] / dy; }
 
-    std::vector<unsigned char> blob;
-    size_t o_twx = blob.size();
+    to.twx = blob.size();
     if (fp64) push_complex<double>(blob, cx, sx); else push_complex<float>(blob, cx, sx);
     pad_blob(blob);
-    size_t o_twy = blob.size();
+    to.twy = blob.size();
     if (fp64) push_complex<double>(blob, cy, sy); else push_complex<float>(blob, cy, sy);
     pad_blob(blob);
-    size_t o_sv = blob.size(); push_doubles(blob, svol); pad_blob(blob);
-    size_t o_rl = blob.size(); push_doubles(blob, rflo); pad_blob(blob);
-    size_t o_rh = blob.size(); push_doubles(blob, rfhi); pad_blob(blob);
-    size_t o_a = blob.size(); push_doubles(blob, acoef); pad_blob(blob);
-    size_t o_iz = blob.size(); push_doubles(blob, idzn); pad_blob(blob);
-    size_t o_lx = blob.size(); push_doubles(blob, lamx); pad_blob(blob);
-    size_t o_ly = blob.size(); push_doubles(blob, lamy); pad_blob(blob);
-    size_t o_ex = blob.size();
+    to.sv = blob.size(); push_doubles(blob, svol); pad_blob(blob);
+    to.rl = blob.size(); push_doubles(blob, rflo); pad_blob(blob);
+    to.rh = blob.size(); push_doubles(blob, rfhi); pad_blob(blob);
+    to.a = blob.size(); push_doubles(blob, acoef); pad_blob(blob);
+    to.iz = blob.size(); push_doubles(blob, idzn); pad_blob(blob);
+    to.lx = blob.size(); push_doubles(blob, lamx); pad_blob(blob);
+    to.ly = blob.size(); push_doubles(blob, lamy); pad_blob(blob);
+    to.ex = blob.size();
     if (fp64) push_complex<double>(blob, exr, exi); else push_complex<float>(blob, exr, exi);
     pad_blob(blob);
-    size_t o_ey = blob.size();
+    to.ey = blob.size();
     if (fp64) push_complex<double>(blob, eyr, eyi); else push_complex<float>(blob, eyr, eyi);
     pad_blob(blob);
-    size_t o_err = blob.size();
+    to.err = blob.size();
     blob.resize(blob.size() + 256, 0);
-
-    void* d = nullptr;
-    if (cudaMalloc(&d, blob.size()) != cudaSuccess) { cudaGetLastError(); delete p; return MONC_PROJ_ENOMEM; }
-    cudaStream_t st = (cudaStream_t)stream;
-    if (cudaMemcpyAsync(d, blob.data(), blob.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess) {
-        cudaFree(d); delete p; return MONC_PROJ_ECUDA;
-    }
-    unsigned char* db = (unsigned char*)d;
-    p->dev_tables = d;
-    p->twx = db + o_twx; p->twy = db + o_twy;
-    p->svol = (const double*)(db + o_sv); p->rflo = (const double*)(db + o_rl);
-    p->rfhi = (const double*)(db + o_rh); p->acoef = (const double*)(db + o_a);
-    p->idzn = (const double*)(db + o_iz); p->lamx = (const double*)(db + o_lx);
-    p->lamy = (const double*)(db + o_ly); p->ex = db + o_ex; p->ey = db + o_ey;
-    p->err = (int*)(db + o_err);
 
     // ---- task shapes
     p->bs_row = nx;
@@ -343,6 +317,59 @@ int monc_proj_plan(monc_proj_plan_t* out, int nx, int ny, int nz, double dx, dou
     p->off_Y = off; off = align256(off + L * 16);
     p->off_Gp = off; off = align256(off + L * 8);
     p->ws_bytes = off;
+}
+
+// Point the plan's table pointers into device memory `db` holding the blob.
+void plan_bind(monc_proj_plan_s* p, unsigned char* db, const TableOffsets& to) {
+    p->twx = db + to.twx; p->twy = db + to.twy;
+    p->svol = (const double*)(db + to.sv); p->rflo = (const double*)(db + to.rl);
+    p->rfhi = (const double*)(db + to.rh); p->acoef = (const double*)(db + to.a);
+    p->idzn = (const double*)(db + to.iz); p->lamx = (const double*)(db + to.lx);
+    p->lamy = (const double*)(db + to.ly); p->ex = db + to.ex; p->ey = db + to.ey;
+    p->err = (int*)(db + to.err);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* monc_proj_status_string(int status) {
+    switch (status) {
+        case MONC_PROJ_OK: return "ok";
+        case MONC_PROJ_EINVAL: return "invalid argument";
+        case MONC_PROJ_EUNSUPPORTED: return "unsupported size (nx, ny must be 2^a 3^b 5^c, <= 4096)";
+        case MONC_PROJ_ENOMEM: return "device allocation failed";
+        case MONC_PROJ_ECUDA: return "CUDA runtime error";
+        case MONC_PROJ_ETIMEOUT: return "bounded device wait timed out";
+        case MONC_PROJ_EDEVICE: return "device-detected error";
+        default: return "unknown status";
+    }
+}
+
+int monc_proj_plan(monc_proj_plan_t* out, int nx, int ny, int nz, double dx, double dy,
+                   const double* dz, const double* rho_c, const double* rho_f,
+                   int precision, void* stream) {
+    if (!out) return MONC_PROJ_EINVAL;
+    *out = nullptr;
+    const int vr = validate_grid(nx, ny, nz, dx, dy, dz, rho_c, rho_f, precision);
+    if (vr != MONC_PROJ_OK) return vr;
+
+    monc_proj_plan_s* p = new (std::nothrow) monc_proj_plan_s();
+    if (!p) return MONC_PROJ_ENOMEM;
+    std::vector<unsigned char> blob;
+    TableOffsets to{};
+    plan_prepare(p, nx, ny, nz, dx, dy, dz, rho_c, rho_f, precision, blob, to);
+    cudaGetDevice(&p->device);
+
+    void* d = nullptr;
+    if (cudaMalloc(&d, blob.size()) != cudaSuccess) { cudaGetLastError(); delete p; return MONC_PROJ_ENOMEM; }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(d, blob.data(), blob.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaFree(d); delete p; return MONC_PROJ_ECUDA;
+    }
+    p->dev_tables = d;
+    plan_bind(p, (unsigned char*)d, to);
     *out = p;
     return MONC_PROJ_OK;
 }
