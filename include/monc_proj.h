@@ -59,7 +59,8 @@ typedef enum {
     MONC_PROJ_ENOMEM = 3,        /* device allocation failed while building a plan */
     MONC_PROJ_ECUDA = 4,         /* a CUDA runtime call failed (launch, copy) */
     MONC_PROJ_ETIMEOUT = 5,      /* a bounded device wait gave up (latched device error) */
-    MONC_PROJ_EDEVICE = 6        /* another device-detected error (latched device error) */
+    MONC_PROJ_EDEVICE = 6,       /* another device-detected error (latched device error) */
+    MONC_PROJ_ESCRATCH = 7       /* monc_proj_solve_noalloc: problem too large for its static scratch */
 } monc_proj_status;
 
 typedef enum {
@@ -170,6 +171,48 @@ int monc_proj_profile_read(monc_proj_plan_t plan, int max_phases, double* total_
 
 /* Static name of a kernel phase ("fwd_rows", "tridiag", ...), NULL if out of range. */
 const char* monc_proj_phase_name(int phase);
+
+/*
+ * monc_proj_solve_noalloc -- one projection that allocates no device memory.
+ *
+ * The paper has no counterpart; this entry point exists for callers that
+ * cannot allocate: host applications that own every byte of device memory
+ * through their own pool and forbid libraries from calling cudaMalloc, model
+ * components that are handed finished device arrays by their host model and
+ * keep no allocator of their own, and latency-critical loops that cannot
+ * afford cudaMalloc's implicit device-wide synchronisation.  Such a caller
+ * passes only the grid, the host profiles and its device inputs and outputs.
+ *
+ * Everything else the solve needs -- the grid tables (twiddles, modified
+ * wavenumbers, vertical coefficients) and the solve's workspace -- lives in
+ * one static device array of MONC_PROJ_NOALLOC_SCRATCH_BYTES bytes compiled
+ * into this library.  Every process that loads the library holds that array
+ * on every GPU where the library's kernels are loaded, until it exits.
+ *
+ * Arguments are those of monc_proj_plan followed by those of monc_proj_solve
+ * (same layouts, types, alignment and in-place rules); there is no plan and
+ * no workspace argument.  The call is asynchronous on `stream`.
+ *
+ * Limits and behaviour:
+ *  - a grid whose tables plus workspace exceed MONC_PROJ_NOALLOC_SCRATCH_BYTES
+ *    is rejected with MONC_PROJ_ESCRATCH before anything is enqueued (about
+ *    64 x 64 x 64 in FP64 or 80 x 80 x 64 in mixed precision fit);
+ *  - the first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, once per device, with that device current); make
+ *    that first call before any stream capture begins;
+ *  - every call on a device shares the one array and overwrites the previous
+ *    call's tables and workspace: calls whose GPU work overlaps (different
+ *    streams, or different host threads without ordering) race and give wrong
+ *    results.  Calls on one stream are ordered and safe;
+ *  - the tables are uploaded from pageable host memory on `stream` at every
+ *    call; device-detected errors of the call are not reported (there is no
+ *    plan to latch them in).
+ */
+#define MONC_PROJ_NOALLOC_SCRATCH_BYTES (32u << 20)
+int monc_proj_solve_noalloc(int nx, int ny, int nz, double dx, double dy,
+                            const double* dz, const double* rho_c, const double* rho_f,
+                            int precision, const void* u, const void* v, const void* w,
+                            void* u_out, void* v_out, void* w_out, void* phi_out, void* stream);
 
 /* Plan introspection: grid sizes, precision and the FP64-column count of a3. */
 int monc_proj_plan_info(monc_proj_plan_t plan, int* nx, int* ny, int* nz, int* precision,

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -342,6 +343,7 @@ const char* monc_proj_status_string(int status) {
         case MONC_PROJ_ECUDA: return "CUDA runtime error";
         case MONC_PROJ_ETIMEOUT: return "bounded device wait timed out";
         case MONC_PROJ_EDEVICE: return "device-detected error";
+        case MONC_PROJ_ESCRATCH: return "problem too large for the no-alloc static scratch";
         default: return "unknown status";
     }
 }
@@ -494,3 +496,70 @@ int monc_proj_plan_info(monc_proj_plan_t plan, int* nx, int* ny, int* nz, int* p
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// No-alloc entry point: tables and workspace in a static device array.
+// ---------------------------------------------------------------------------
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MONC_PROJ_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_base[kNoallocMaxDevices] = {};
+
+// Device address of the static array on the current device, looked up once
+// per device (with that device current).
+int noalloc_base(void** out, int* device) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return MONC_PROJ_ECUDA; }
+    if (dev < 0 || dev >= kNoallocMaxDevices) return MONC_PROJ_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) { cudaGetLastError(); return MONC_PROJ_ECUDA; }
+        g_noalloc_base[dev] = ptr;
+    }
+    *out = g_noalloc_base[dev];
+    *device = dev;
+    return MONC_PROJ_OK;
+}
+
+}  // namespace
+
+extern "C" int monc_proj_solve_noalloc(int nx, int ny, int nz, double dx, double dy,
+                                       const double* dz, const double* rho_c, const double* rho_f,
+                                       int precision, const void* u, const void* v, const void* w,
+                                       void* u_out, void* v_out, void* w_out, void* phi_out,
+                                       void* stream) {
+    const int vr = validate_grid(nx, ny, nz, dx, dy, dz, rho_c, rho_f, precision);
+    if (vr != MONC_PROJ_OK) return vr;
+    if (!u || !v || !w || !u_out || !v_out || !w_out) return MONC_PROJ_EINVAL;
+    const void* ptrs[] = {u, v, w, u_out, v_out, w_out, phi_out};
+    for (const void* x : ptrs)
+        if (((uintptr_t)x) & 15) return MONC_PROJ_EINVAL;
+
+    monc_proj_plan_s plan{};
+    std::vector<unsigned char> blob;
+    TableOffsets to{};
+    plan_prepare(&plan, nx, ny, nz, dx, dy, dz, rho_c, rho_f, precision, blob, to);
+    const size_t tables = align256(blob.size());
+    if (tables + plan.ws_bytes > (size_t)MONC_PROJ_NOALLOC_SCRATCH_BYTES) return MONC_PROJ_ESCRATCH;
+
+    void* base = nullptr;
+    const int br = noalloc_base(&base, &plan.device);
+    if (br != MONC_PROJ_OK) return br;
+    cudaStream_t st = (cudaStream_t)stream;
+    // The blob carries a zeroed device error word, so every call starts clean.
+    if (cudaMemcpyAsync(base, blob.data(), blob.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        cudaGetLastError();
+        return MONC_PROJ_ECUDA;
+    }
+    unsigned char* b = (unsigned char*)base;
+    plan_bind(&plan, b, to);
+    const ProjParams q = make_params(&plan, u, v, w, u_out, v_out, w_out, phi_out, b + tables);
+    if (plan.precision == MONC_PROJ_FP64) return launch_solve<double>(&plan, q, st);
+    return launch_solve<float>(&plan, q, st);
+}

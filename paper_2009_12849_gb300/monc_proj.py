@@ -25,6 +25,8 @@ MONC_PROJ_ENOMEM = 3
 MONC_PROJ_ECUDA = 4
 MONC_PROJ_ETIMEOUT = 5
 MONC_PROJ_EDEVICE = 6
+MONC_PROJ_ESCRATCH = 7
+MONC_PROJ_NOALLOC_SCRATCH_BYTES = 32 << 20
 MONC_PROJ_FP64 = 0
 MONC_PROJ_MIXED = 1
 
@@ -36,6 +38,7 @@ EXPORTS = [
     "monc_proj_batch_workspace_size", "monc_proj_solve_batch", "monc_proj_sync_status",
     "monc_proj_destroy", "monc_proj_status_string", "monc_proj_plan_info",
     "monc_proj_profile", "monc_proj_profile_read", "monc_proj_phase_name",
+    "monc_proj_solve_noalloc",
 ]
 
 
@@ -81,6 +84,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.monc_proj_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_double), ip, ip]
     L.monc_proj_phase_name.argtypes = [i]
     L.monc_proj_phase_name.restype = ctypes.c_char_p
+    L.monc_proj_solve_noalloc.argtypes = [i, i, i, d, d, dp, dp, dp, i, vp, vp, vp, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("monc_proj_status_string", "monc_proj_phase_name"):
             getattr(L, name).restype = ctypes.c_int
@@ -197,6 +201,21 @@ def monc_proj_profile_read(plan: int) -> dict:
                                                  ctypes.byref(ns)), "monc_proj_profile_read")
     return {"solves": ns.value,
             "phases": {monc_proj_phase_name(i): buf[i] for i in range(nph.value)}}
+
+
+def monc_proj_solve_noalloc(nx, ny, nz, dx, dy, dz, rho_c, rho_f, precision, u, v, w,
+                            u_out, v_out, w_out, phi_out=None, stream=None):
+    """One projection that allocates no device memory (static scratch in the library).
+
+    For callers that cannot allocate device memory themselves or let a library
+    do so; see the header for the size limit and the sharing rules."""
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    ptr = lambda t: ctypes.c_void_p(None if t is None else t.data_ptr())
+    rc = load_library().monc_proj_solve_noalloc(
+        int(nx), int(ny), int(nz), float(dx), float(dy), _dbl(dz), _dbl(rho_c), _dbl(rho_f), prec,
+        ptr(u), ptr(v), ptr(w), ptr(u_out), ptr(v_out), ptr(w_out), ptr(phi_out),
+        ctypes.c_void_p(_stream_handle(stream)))
+    _check(rc, "monc_proj_solve_noalloc")
 
 
 # ----------------------------------------------------------------- convenience
