@@ -1,4 +1,4 @@
-// Batched mixed-radix (2,3,4,5,8) complex FFT in shared memory.
+// Batched mixed-radix (2,3,4,5,8,16,32) complex FFT in shared memory.
 //
 // Steps a2 and a4 of the projection (paper, Section 4: a forward FFT on every
 // level and a backward FFT) need length-nx transforms along x and length-ny
@@ -8,9 +8,13 @@
 // is needed.  One stage of radix R with Ns = product of the radices already
 // applied processes n/R butterflies: butterfly q reads elements q + r n/R,
 // multiplies element r by W_{Ns R}^{r (q mod Ns)}, takes a length-R DFT and
-// writes element r to (q div Ns) Ns R + (q mod Ns) + r Ns.
+// writes element r to (q div Ns) Ns R + (q mod Ns) + r Ns.  Radices 16 and 32
+// run as compile-time register DFTs (regfft.cuh), so a length-1024 transform
+// takes two passes through shared memory.
 #pragma once
 #include <cuda_runtime.h>
+
+#define MP_HD __host__ __device__ __forceinline__
 
 namespace mp {
 
@@ -19,39 +23,32 @@ template <> struct CT<double> { using T = double2; };
 template <> struct CT<float> { using T = float2; };
 template <typename R> using cplx = typename CT<R>::T;
 
-template <typename R> __device__ __forceinline__ cplx<R> cmk(R x, R y) { cplx<R> c; c.x = x; c.y = y; return c; }
-template <typename C> __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
-template <typename C> __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
-template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+template <typename R> MP_HD cplx<R> cmk(R x, R y) { cplx<R> c; c.x = x; c.y = y; return c; }
+template <typename C> MP_HD C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> MP_HD C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C> MP_HD C cmul(C a, C b) {
     C c; c.x = a.x * b.x - a.y * b.y; c.y = a.x * b.y + a.y * b.x; return c;
 }
 // a * conj(b)
-template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
+template <typename C> MP_HD C cmulc(C a, C b) {
     C c; c.x = a.x * b.x + a.y * b.y; c.y = a.y * b.x - a.x * b.y; return c;
 }
-template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) { a.x *= s; a.y *= s; return a; }
-template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+template <typename C, typename R> MP_HD C cscale(C a, R s) { a.x *= s; a.y *= s; return a; }
+template <typename C> MP_HD C cconj(C a) { a.y = -a.y; return a; }
 // multiply by s*i, s = +1 or -1
-template <typename C> __device__ __forceinline__ C cmul_si(C a, int s) {
+template <typename C> MP_HD C cmul_si(C a, int s) {
     C c; if (s > 0) { c.x = -a.y; c.y = a.x; } else { c.x = a.y; c.y = -a.x; } return c;
 }
 
-// Radix plan of one transform length.
-struct FftFactors {
-    int n;
-    int nstages;
-    int radix[24];
-};
-
 // Length-R DFTs on registers, exponent sign S (-1 forward, +1 inverse).
 template <typename R, int S> struct Dft2 {
-    static __device__ __forceinline__ void run(cplx<R>* x) {
+    static MP_HD void run(cplx<R>* x) {
         cplx<R> a = x[0], b = x[1];
         x[0] = cadd(a, b); x[1] = csub(a, b);
     }
 };
 template <typename R, int S> struct Dft4 {
-    static __device__ __forceinline__ void run(cplx<R>* x) {
+    static MP_HD void run(cplx<R>* x) {
         cplx<R> s02 = cadd(x[0], x[2]), d02 = csub(x[0], x[2]);
         cplx<R> s13 = cadd(x[1], x[3]), d13 = cmul_si(csub(x[1], x[3]), S);
         x[0] = cadd(s02, s13); x[2] = csub(s02, s13);
@@ -59,7 +56,7 @@ template <typename R, int S> struct Dft4 {
     }
 };
 template <typename R, int S> struct Dft8 {
-    static __device__ __forceinline__ void run(cplx<R>* x) {
+    static MP_HD void run(cplx<R>* x) {
         const R h = (R)0.70710678118654752440;   // 1/sqrt(2)
         cplx<R> e[4] = {x[0], x[2], x[4], x[6]};
         cplx<R> o[4] = {x[1], x[3], x[5], x[7]};
@@ -76,7 +73,7 @@ template <typename R, int S> struct Dft8 {
     }
 };
 template <typename R, int S> struct Dft3 {
-    static __device__ __forceinline__ void run(cplx<R>* x) {
+    static MP_HD void run(cplx<R>* x) {
         const R c = (R)0.86602540378443864676;   // sqrt(3)/2
         cplx<R> t = cadd(x[1], x[2]);
         cplx<R> d = csub(x[1], x[2]);
@@ -88,7 +85,7 @@ template <typename R, int S> struct Dft3 {
     }
 };
 template <typename R, int S> struct Dft5 {
-    static __device__ __forceinline__ void run(cplx<R>* x) {
+    static MP_HD void run(cplx<R>* x) {
         const R c1 = (R)0.30901699437494742410;    // cos(2 pi/5) = (sqrt5-1)/4
         const R c2 = (R)-0.80901699437494742410;   // cos(4 pi/5) = -(sqrt5+1)/4
         const R s1 = (R)0.95105651629515357212;    // sin(2 pi/5)
@@ -105,41 +102,72 @@ template <typename R, int S> struct Dft5 {
     }
 };
 
-template <typename R, int RAD, int S> struct DftSel;
-template <typename R, int S> struct DftSel<R, 2, S> { using T = Dft2<R, S>; };
-template <typename R, int S> struct DftSel<R, 3, S> { using T = Dft3<R, S>; };
-template <typename R, int S> struct DftSel<R, 4, S> { using T = Dft4<R, S>; };
-template <typename R, int S> struct DftSel<R, 5, S> { using T = Dft5<R, S>; };
-template <typename R, int S> struct DftSel<R, 8, S> { using T = Dft8<R, S>; };
+}  // namespace mp
 
+#include "regfft.cuh"
+
+namespace mp {
+
+// Division by a run-time constant d as a multiply-high and shift (the
+// round-up method of Granlund and Montgomery, "Division by invariant integers
+// using multiplication", 1994): q = (umulhi(t, m) + t) >> s with
+// s = ceil(log2 d), m = floor(2^32 (2^s - d) / d) + 1, exact for t < 2^31.
+struct FastDiv {
+    unsigned m, s;
+};
+__device__ __forceinline__ unsigned fdiv(unsigned t, FastDiv f) { return (__umulhi(t, f.m) + t) >> f.s; }
+
+// One Stockham stage: radix R applied with Ns = product of the earlier radices.
+struct FftStage {
+    int radix, ns, nq;           // nq = n / R
+    FastDiv fq, fns;             // division by nq and by Ns
+};
+
+// Radix plan of one transform length (largest radices first).
+struct FftFactors {
+    int n;
+    int nstages;
+    FftStage st[16];
+};
+
+// Shared-memory index of element i of a transform: one pad element every 32
+// keeps the stride-R accesses of the first stages free of bank conflicts.
+__device__ __forceinline__ int spad(int i) { return i + (i >> 5); }
+__host__ __device__ inline int spad_len(int n) { return n + (n >> 5) + 1; }
+
+// Twiddle tables: stage s of a length-n plan owns entries [s*n, s*n + R*Ns)
+// of the plan's table, laid out [r][k]: entry r*Ns + k = W_{Ns R}^{r k}, so
+// that threads with consecutive k read consecutive entries.
+//
 // One Stockham stage over `nb` transforms: element e of transform b sits at
-// base[b*bstride + e].  tw[m] = exp(-2 pi i m / n).
+// base[b*bstride + spad(e)]; tw points at this stage's table.
 template <typename R, int RAD, int S>
 __device__ __forceinline__ void fft_stage(const cplx<R>* __restrict__ in, cplx<R>* __restrict__ out,
-                                          int n, int Ns, int nb, int bstride,
+                                          const FftStage& st, int nb, int bstride,
                                           const cplx<R>* __restrict__ tw) {
-    const int nq = n / RAD;
+    const int nq = st.nq, Ns = st.ns;
     const int total = nq * nb;
-    const int tstep = n / (Ns * RAD);
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int b = t / nq;
+        const int b = (int)fdiv((unsigned)t, st.fq);
         const int q = t - b * nq;
-        const int k = q % Ns;
-        const cplx<R>* src = in + b * bstride + q;
+        const int qd = (int)fdiv((unsigned)q, st.fns);
+        const int k = q - qd * Ns;
+        const cplx<R>* src = in + b * bstride;
         cplx<R> x[RAD];
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) x[r] = src[r * nq];
+        for (int r = 0; r < RAD; ++r) x[r] = src[spad(q + r * nq)];
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < RAD; ++r) {
-                cplx<R> wv = tw[r * k * tstep];
+                const cplx<R> wv = __ldg(&tw[r * Ns + k]);
                 x[r] = (S < 0) ? cmul(x[r], wv) : cmulc(x[r], wv);
             }
         }
-        DftSel<R, RAD, S>::T::run(x);
-        cplx<R>* dst = out + b * bstride + (q / Ns) * Ns * RAD + k;
+        RegFFT<R, RAD, S>::run(x);
+        cplx<R>* dst = out + b * bstride;
+        const int base = qd * Ns * RAD + k;
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) dst[r * Ns] = x[r];
+        for (int r = 0; r < RAD; ++r) dst[spad(base + r * Ns)] = x[r];
     }
 }
 
@@ -149,21 +177,232 @@ __device__ __forceinline__ void fft_stage(const cplx<R>* __restrict__ in, cplx<R
 template <typename R, int S>
 __device__ cplx<R>* fft_batch(cplx<R>* a, cplx<R>* b, int nb, int bstride,
                               const FftFactors& f, const cplx<R>* __restrict__ tw) {
-    int Ns = 1;
     for (int s = 0; s < f.nstages; ++s) {
-        const int rad = f.radix[s];
-        switch (rad) {
-            case 8: fft_stage<R, 8, S>(a, b, f.n, Ns, nb, bstride, tw); break;
-            case 4: fft_stage<R, 4, S>(a, b, f.n, Ns, nb, bstride, tw); break;
-            case 2: fft_stage<R, 2, S>(a, b, f.n, Ns, nb, bstride, tw); break;
-            case 5: fft_stage<R, 5, S>(a, b, f.n, Ns, nb, bstride, tw); break;
-            default: fft_stage<R, 3, S>(a, b, f.n, Ns, nb, bstride, tw); break;
+        const FftStage& st = f.st[s];
+        switch (st.radix) {
+            case 32:
+                if constexpr (sizeof(R) == 4) fft_stage<R, 32, S>(a, b, st, nb, bstride, tw + s * f.n);
+                break;
+            case 16: fft_stage<R, 16, S>(a, b, st, nb, bstride, tw + s * f.n); break;
+            case 8: fft_stage<R, 8, S>(a, b, st, nb, bstride, tw + s * f.n); break;
+            case 4: fft_stage<R, 4, S>(a, b, st, nb, bstride, tw + s * f.n); break;
+            case 2: fft_stage<R, 2, S>(a, b, st, nb, bstride, tw + s * f.n); break;
+            case 5: fft_stage<R, 5, S>(a, b, st, nb, bstride, tw + s * f.n); break;
+            default: fft_stage<R, 3, S>(a, b, st, nb, bstride, tw + s * f.n); break;
         }
         __syncthreads();
         cplx<R>* t = a; a = b; b = t;
-        Ns *= rad;
     }
     return a;
+}
+
+// ---------------------------------------------------------------------------
+// Compile-time plans for the common lengths.  Every stage's radix, Ns, n/R
+// and twiddle stride are constants; every thread holds at most E elements of
+// a stage (its ceil(E/R) butterflies) in registers, the block synchronises,
+// and the outputs overwrite the inputs in the single shared buffer.  The
+// caller sizes the block so that blockDim.x * E >= nb * N.
+// ---------------------------------------------------------------------------
+template <typename R> struct ElemsPerThread { static constexpr int value = sizeof(R) == 4 ? 32 : 16; };
+
+// Radix of the next stage for the remaining length M (largest first).
+template <typename R, int M> struct NextRadix {
+    static constexpr int maxr = sizeof(R) == 4 ? 32 : 16;
+    static constexpr int value = (maxr >= 32 && M % 32 == 0) ? 32 : (M % 16 == 0) ? 16 : (M % 8 == 0) ? 8
+                               : (M % 4 == 0) ? 4 : (M % 2 == 0) ? 2 : (M % 5 == 0) ? 5 : 3;
+};
+
+// Position of the stage with the given Ns in the compile-time plan.
+template <typename R, int N> constexpr int stage_index_impl(int target) {
+    int ns = 1, s = 0;
+    while (ns < target) {
+        const int m = N / ns;
+        const int maxr = sizeof(R) == 4 ? 32 : 16;
+        const int rad = (maxr >= 32 && m % 32 == 0) ? 32 : (m % 16 == 0) ? 16 : (m % 8 == 0) ? 8
+                      : (m % 4 == 0) ? 4 : (m % 2 == 0) ? 2 : (m % 5 == 0) ? 5 : 3;
+        ns *= rad;
+        ++s;
+    }
+    return s;
+}
+template <typename R, int N, int NS> struct StageIndex {
+    static constexpr int value = stage_index_impl<R, N>(NS);
+};
+
+template <typename R, int N, int NS, int S>
+__device__ __forceinline__ void ct_stage(cplx<R>* buf, int nb, int bstride, const cplx<R>* __restrict__ tws) {
+    const cplx<R>* __restrict__ tw = tws + StageIndex<R, N, NS>::value * N;
+    constexpr int RAD = NextRadix<R, N / NS>::value;
+    constexpr int E = ElemsPerThread<R>::value;
+    constexpr int NB = (E + RAD - 1) / RAD;
+    constexpr int NQ = N / RAD;
+    const int total = NQ * nb;
+    cplx<R> x[NB][RAD];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int t = threadIdx.x + i * blockDim.x;
+        if (t < total) {
+            const int b = t / NQ;
+            const int q = t - b * NQ;
+            const cplx<R>* src = buf + b * bstride;
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) x[i][r] = src[spad(q + r * NQ)];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int t = threadIdx.x + i * blockDim.x;
+        if (t < total) {
+            const int b = t / NQ;
+            const int q = t - b * NQ;
+            const int qd = q / NS;
+            const int k = q - qd * NS;
+            if (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < RAD; ++r) {
+                    const cplx<R> wv = __ldg(&tw[r * NS + k]);
+                    x[i][r] = (S < 0) ? cmul(x[i][r], wv) : cmulc(x[i][r], wv);
+                }
+            }
+            RegFFT<R, RAD, S>::run(x[i]);
+            cplx<R>* dst = buf + b * bstride;
+            const int base = qd * NS * RAD + k;
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) dst[spad(base + r * NS)] = x[i][r];
+        }
+    }
+    __syncthreads();
+}
+
+template <typename R, int N, int NS, int S> struct CtFFT {
+    static __device__ __forceinline__ void run(cplx<R>* buf, int nb, int bstride, const cplx<R>* tw) {
+        ct_stage<R, N, NS, S>(buf, nb, bstride, tw);
+        CtFFT<R, N, NS * NextRadix<R, N / NS>::value, S>::run(buf, nb, bstride, tw);
+    }
+};
+template <typename R, int N, int S> struct CtFFT<R, N, N, S> {
+    static __device__ __forceinline__ void run(cplx<R>*, int, int, const cplx<R>*) {}
+};
+
+// ---------------------------------------------------------------------------
+// First and last stages fused with the caller's global loads and stores.
+// The first stage (Ns = 1) takes its inputs from load(b, e) straight into
+// registers and writes its outputs to shared memory; the last stage reads
+// shared memory and hands each butterfly's outputs to store(b, q, x, NS):
+// x[r] is element q + r*NS of transform b.  The middle
+// stages run as above.  BFAST selects the butterfly-to-thread map:
+// consecutive threads take consecutive transforms (columns of a tile, whose
+// global elements are adjacent) or consecutive butterflies of one transform
+// (rows, whose elements are adjacent).
+// ---------------------------------------------------------------------------
+template <typename R, int N, int NS> struct StageInfo {
+    static constexpr int RAD = NextRadix<R, N / NS>::value;
+    static constexpr int NQ = N / RAD;
+    static constexpr int NEXT = NS * RAD;
+    static constexpr bool LAST = (NEXT == N);
+};
+
+template <typename R, int N> constexpr int last_stage_ns_impl() {
+    int ns = 1;
+    while (ns < N) {
+        const int m = N / ns;
+        const int maxr = sizeof(R) == 4 ? 32 : 16;
+        const int rad = (maxr >= 32 && m % 32 == 0) ? 32 : (m % 16 == 0) ? 16 : (m % 8 == 0) ? 8
+                      : (m % 4 == 0) ? 4 : (m % 2 == 0) ? 2 : (m % 5 == 0) ? 5 : 3;
+        if (ns * rad == N) return ns;
+        ns *= rad;
+    }
+    return ns;
+}
+
+// Ns of the last stage of the compile-time plan for length N.
+template <typename R, int N> struct LastNs {
+    static constexpr int value = last_stage_ns_impl<R, N>();
+};
+
+template <bool BFAST, int NQ>
+__device__ __forceinline__ void bfly_map(int t, int nb, int& b, int& q) {
+    if (BFAST) { q = t / nb; b = t - q * nb; }
+    else { b = t / NQ; q = t - b * NQ; }
+}
+
+template <typename R, int N, int S, bool BFAST, class Load>
+__device__ __forceinline__ void ct_first(cplx<R>* buf, int nb, int bstride, Load&& load) {
+    using SI = StageInfo<R, N, 1>;
+    constexpr int RAD = SI::RAD, NQ = SI::NQ;
+    constexpr int E = ElemsPerThread<R>::value;
+    constexpr int NB = (E + RAD - 1) / RAD;
+    const int total = NQ * nb;
+    cplx<R> x[NB][RAD];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int t = threadIdx.x + i * blockDim.x;
+        if (t < total) {
+            int b, q;
+            bfly_map<BFAST, NQ>(t, nb, b, q);
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) x[i][r] = load(b, q + r * NQ);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int t = threadIdx.x + i * blockDim.x;
+        if (t < total) {
+            int b, q;
+            bfly_map<BFAST, NQ>(t, nb, b, q);
+            RegFFT<R, RAD, S>::run(x[i]);
+            cplx<R>* dst = buf + b * bstride;
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) dst[spad(q * RAD + r)] = x[i][r];
+        }
+    }
+    __syncthreads();
+}
+
+template <typename R, int N, int NS, int S, bool STOP = StageInfo<R, N, NS>::LAST> struct CtMid {
+    static __device__ __forceinline__ void run(cplx<R>* buf, int nb, int bstride, const cplx<R>* tw) {
+        ct_stage<R, N, NS, S>(buf, nb, bstride, tw);
+        CtMid<R, N, StageInfo<R, N, NS>::NEXT, S>::run(buf, nb, bstride, tw);
+    }
+};
+template <typename R, int N, int NS, int S> struct CtMid<R, N, NS, S, true> {
+    static __device__ __forceinline__ void run(cplx<R>*, int, int, const cplx<R>*) {}
+};
+
+template <typename R, int N, int S, bool BFAST, class Store>
+__device__ __forceinline__ void ct_last(const cplx<R>* buf, int nb, int bstride, const cplx<R>* __restrict__ tws,
+                                        Store&& store) {
+    constexpr int NS = LastNs<R, N>::value;
+    const cplx<R>* __restrict__ tw = tws + StageIndex<R, N, NS>::value * N;
+    using SI = StageInfo<R, N, NS>;
+    static_assert(SI::LAST, "last stage");
+    constexpr int RAD = SI::RAD, NQ = SI::NQ;
+    constexpr int E = ElemsPerThread<R>::value;
+    constexpr int NB = (E + RAD - 1) / RAD;
+    const int total = NQ * nb;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int t = threadIdx.x + i * blockDim.x;
+        if (t < total) {
+            int b, q;
+            bfly_map<BFAST, NQ>(t, nb, b, q);
+            const cplx<R>* src = buf + b * bstride;
+            cplx<R> x[RAD];
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) x[r] = src[spad(q + r * NQ)];
+            // last stage: Ns * RAD = N, so q < Ns and q is the twiddle index k
+            if (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < RAD; ++r) {
+                    const cplx<R> wv = __ldg(&tw[r * NS + q]);
+                    x[r] = (S < 0) ? cmul(x[r], wv) : cmulc(x[r], wv);
+                }
+            }
+            RegFFT<R, RAD, S>::run(x);
+            store(b, q, x, NS);
+        }
+    }
 }
 
 }  // namespace mp

@@ -14,13 +14,19 @@ namespace mp {
 struct ProjParams {
     int nx, ny, nz, nxh, nxp;
     FftFactors fx, fy;
-    const void* twx;            // [nx] exp(-2 pi i m/nx), storage precision
-    const void* twy;            // [ny]
+    const void* twx;            // per-stage twiddle tables of the x plan (storage precision)
+    const void* twy;            // per-stage twiddle tables of the y plan
     const double* svol;         // [nz]   rho_c[k] dz[k]
     const double* rflo;         // [nz]   rho_f[k]   (0 at k = 0)
     const double* rfhi;         // [nz]   rho_f[k+1] (0 at k = nz-1)
     const double* acoef;        // [nz+1] A[k] = rho_f[k]/dzn[k], A[0] = A[nz] = 0
     const double* idzn;         // [nz+1] 1/dzn[k] (0 at k = 0, nz)
+    const double* csum;         // [nz]   A[k] + A[k+1]
+    const float* svol32;        // FP32 copies of svol, acoef, csum, idzn
+    const float* acoef32;
+    const float* csum32;
+    const float* idzn32;
+    double lam_fp64;            // mixed plans: |lambda| below which a column runs in FP64
     const double* lamx;         // [nxh]  2(cos(2 pi kx/nx) - 1)/dx^2
     const double* lamy;         // [ny]
     const void* ex;             // [nxh]  (exp(2 pi i kx/nx) - 1)/dx, storage precision
@@ -37,7 +43,7 @@ struct ProjParams {
     // task shapes
     int rows_fwd;               // real rows per forward row task (even)
     int nrb_fwd;                // row tasks per level (forward)
-    int rows_inv;               // real rows per inverse row task
+    int rows_inv;               // real rows per inverse row task (even)
     int nrb_inv;
     int nch;                    // real channels per row in the inverse (3, or 4 with phi)
     int tw_cols;                // kx columns per column task
@@ -48,6 +54,24 @@ struct ProjParams {
 
 template <typename R> __device__ __forceinline__ const cplx<R>* ctab(const void* p) { return (const cplx<R>*)p; }
 
+// Elements whose global loads one thread issues before using any of them.
+constexpr int kLoadBatch = 8;
+
+// Transform nb sequences held in shared memory at buf[b*bs + spad(e)].
+// N > 0: compile-time in-place plan (one buffer); N == 0: run-time plan,
+// ping-pong with a second buffer right after the first.  Returns the buffer
+// holding the result.
+template <typename R, int N, int S>
+__device__ __forceinline__ cplx<R>* run_fft(cplx<R>* buf, int nb, int bs, const FftFactors& f,
+                                            const cplx<R>* __restrict__ tw) {
+    if constexpr (N == 0) {
+        return fft_batch<R, S>(buf, buf + nb * bs, nb, bs, f, tw);
+    } else {
+        CtFFT<R, N, 1, S>::run(buf, nb, bs, tw);
+        return buf;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // a1 + a2 (x part): divergence of a block of rows, real FFT along x.
 // Two real rows share one complex transform: z = d_j + i d_{j+1}; after the
@@ -55,8 +79,8 @@ template <typename R> __device__ __forceinline__ const cplx<R>* ctab(const void*
 // Output is the level's x-spectrum in T, scaled by rho_c dz (the symmetric
 // form of the vertical operator).
 // ---------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(256) k_fwd_rows(ProjParams p) {
+template <typename R, int NX>
+__global__ void __launch_bounds__(512) k_fwd_rows(ProjParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using C = cplx<R>;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
@@ -66,7 +90,6 @@ __global__ void __launch_bounds__(256) k_fwd_rows(ProjParams p) {
     const int npair = p.rows_fwd / 2;
     const int bs = p.bs_row;
     C* bufA = (C*)smem_raw;
-    C* bufB = bufA + npair * bs;
 
     const R* u = (const R*)p.u;
     const R* v = (const R*)p.v;
@@ -77,26 +100,51 @@ __global__ void __launch_bounds__(256) k_fwd_rows(ProjParams p) {
     const R rhi = (R)p.rfhi[k];
     const R idx = (R)p.idx, idy = (R)p.idy;
 
-    const int tot = p.rows_fwd * nx;
-    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-        const int r = t / nx;
-        const int i = t - r * nx;
-        const int j = j0 + r;
-        R d = (R)0;
-        if (j < ny) {
-            const size_t row = (size_t)k * plane + (size_t)j * nx;
-            const size_t rowm = (size_t)k * plane + (size_t)(j == 0 ? ny - 1 : j - 1) * nx;
-            const int im = (i == 0) ? nx - 1 : i - 1;
-            R hdiv = (u[row + i] - u[row + im]) * idx + (v[row + i] - v[rowm + i]) * idy;
-            R wl = (k > 0) ? w[row + i] : (R)0;
-            R wh = (k < nz - 1) ? w[row + plane + i] : (R)0;
-            d = sv * hdiv + (rhi * wh - rlo * wl);
+    const C* res;
+    {
+        // Loads are batched (kLoadBatch elements per thread issued before any is
+        // used) so that enough bytes are in flight to cover DRAM latency.
+        const int tot = p.rows_fwd * nx;
+        const int step = kLoadBatch * blockDim.x;
+        for (int base = threadIdx.x; base < tot; base += step) {
+            R uc[kLoadBatch], um[kLoadBatch], vc[kLoadBatch], vm[kLoadBatch], wl[kLoadBatch], wh[kLoadBatch];
+#pragma unroll
+            for (int c = 0; c < kLoadBatch; ++c) {
+                const int t = base + c * blockDim.x;
+                uc[c] = um[c] = vc[c] = vm[c] = wl[c] = wh[c] = (R)0;
+                if (t < tot) {
+                    const int r = (NX > 0) ? t / NX : t / nx;
+                    const int i = t - r * nx;
+                    const int j = j0 + r;
+                    if (j < ny) {
+                        const size_t row = (size_t)k * plane + (size_t)j * nx;
+                        const size_t rowm = (size_t)k * plane + (size_t)(j == 0 ? ny - 1 : j - 1) * nx;
+                        const int im = (i == 0) ? nx - 1 : i - 1;
+                        uc[c] = u[row + i];
+                        um[c] = u[row + im];
+                        vc[c] = v[row + i];
+                        vm[c] = v[rowm + i];
+                        if (k > 0) wl[c] = w[row + i];
+                        if (k < nz - 1) wh[c] = w[row + plane + i];
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < kLoadBatch; ++c) {
+                const int t = base + c * blockDim.x;
+                if (t < tot) {
+                    const int r = (NX > 0) ? t / NX : t / nx;
+                    const int i = t - r * nx;
+                    const R hdiv = (uc[c] - um[c]) * idx + (vc[c] - vm[c]) * idy;
+                    const R d = sv * hdiv + (rhi * wh[c] - rlo * wl[c]);
+                    R* slot = (R*)&bufA[(r >> 1) * bs + spad(i)];
+                    slot[r & 1] = d;
+                }
+            }
         }
-        R* slot = (R*)&bufA[(r >> 1) * bs + i];
-        slot[r & 1] = d;
+        __syncthreads();
+        res = run_fft<R, NX, -1>(bufA, npair, bs, p.fx, ctab<R>(p.twx));
     }
-    __syncthreads();
-    C* res = fft_batch<R, -1>(bufA, bufB, npair, bs, p.fx, ctab<R>(p.twx));
 
     C* T = (C*)p.T;
     const int nxh = p.nxh;
@@ -105,8 +153,8 @@ __global__ void __launch_bounds__(256) k_fwd_rows(ProjParams p) {
         const int q = t / nxh;
         const int kx = t - q * nxh;
         const int j = j0 + 2 * q;
-        C z = res[q * bs + kx];
-        C zc = cconj(res[q * bs + (kx == 0 ? 0 : nx - kx)]);
+        C z = res[q * bs + spad(kx)];
+        C zc = cconj(res[q * bs + spad(kx == 0 ? 0 : nx - kx)]);
         C a = cscale(cadd(z, zc), (R)0.5);
         C dd = csub(z, zc);
         C b = cmk<R>((R)0.5 * dd.y, (R)-0.5 * dd.x);
@@ -125,16 +173,30 @@ __device__ __forceinline__ void load_cols(cplx<R>* buf, const cplx<R>* src, int 
                                           const cplx<R>* mul_y) {
     const int tw = p.tw_cols, ny = p.ny, bs = p.bs_col;
     const int tot = ny * tw;
-    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-        const int j = t / tw;
-        const int c = t - j * tw;
-        const int kx = kx0 + c;
-        cplx<R> val = cmk<R>((R)0, (R)0);
-        if (kx < p.nxh) {
-            val = src[((size_t)k * ny + j) * p.nxp + kx];
-            if (mul_y) val = cmul(val, mul_y[j]);
+    const int step = 2 * kLoadBatch * blockDim.x;
+    for (int base = threadIdx.x; base < tot; base += step) {
+        cplx<R> val[2 * kLoadBatch];
+#pragma unroll
+        for (int c = 0; c < 2 * kLoadBatch; ++c) {
+            const int t = base + c * blockDim.x;
+            val[c] = cmk<R>((R)0, (R)0);
+            if (t < tot) {
+                const int j = t / tw;
+                const int kx = kx0 + (t - j * tw);
+                if (kx < p.nxh) val[c] = src[((size_t)k * ny + j) * p.nxp + kx];
+            }
         }
-        buf[c * bs + j] = val;
+#pragma unroll
+        for (int c = 0; c < 2 * kLoadBatch; ++c) {
+            const int t = base + c * blockDim.x;
+            if (t < tot) {
+                const int j = t / tw;
+                const int cc = t - j * tw;
+                cplx<R> v = val[c];
+                if (mul_y) v = cmul(v, mul_y[j]);
+                buf[cc * bs + spad(j)] = v;
+            }
+        }
     }
 }
 
@@ -146,109 +208,248 @@ __device__ __forceinline__ void store_cols(cplx<R>* dst, const cplx<R>* buf, int
         const int j = t / tw;
         const int c = t - j * tw;
         const int kx = kx0 + c;
-        if (kx < p.nxh) dst[((size_t)k * ny + j) * p.nxp + kx] = buf[c * bs + j];
+        if (kx < p.nxh) dst[((size_t)k * ny + j) * p.nxp + kx] = buf[c * bs + spad(j)];
     }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(256) k_fwd_cols(ProjParams p) {
+template <typename R, int NY>
+__global__ void __launch_bounds__(512) k_fwd_cols(ProjParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using C = cplx<R>;
     const int k = blockIdx.x / p.ntiles;
     const int kx0 = (blockIdx.x - k * p.ntiles) * p.tw_cols;
-    C* bufA = (C*)smem_raw;
-    C* bufB = bufA + p.tw_cols * p.bs_col;
-    load_cols<R>(bufA, (const C*)p.T, k, kx0, p, nullptr);
-    __syncthreads();
-    C* res = fft_batch<R, -1>(bufA, bufB, p.tw_cols, p.bs_col, p.fy, ctab<R>(p.twy));
-    store_cols<R>((C*)p.S, res, k, kx0, p);
+    C* buf = (C*)smem_raw;
+    const C* T = (const C*)p.T;
+    C* S = (C*)p.S;
+    const int nxh = p.nxh, nxp = p.nxp, ny = p.ny;
+    if constexpr (NY > 0) {
+        auto load = [&](int c, int j) -> C {
+            const int kx = kx0 + c;
+            return (kx < nxh) ? T[((size_t)k * ny + j) * nxp + kx] : cmk<R>((R)0, (R)0);
+        };
+        ct_first<R, NY, -1, true>(buf, p.tw_cols, p.bs_col, load);
+        CtMid<R, NY, StageInfo<R, NY, 1>::NEXT, -1>::run(buf, p.tw_cols, p.bs_col, ctab<R>(p.twy));
+        auto store = [&](int c, int q, const C* x, int ns) {
+            const int kx = kx0 + c;
+            if (kx >= nxh) return;
+            constexpr int RAD = StageInfo<R, NY, LastNs<R, NY>::value>::RAD;
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) S[((size_t)k * ny + q + r * ns) * nxp + kx] = x[r];
+        };
+        ct_last<R, NY, -1, true>(buf, p.tw_cols, p.bs_col, ctab<R>(p.twy), store);
+    } else {
+        load_cols<R>(buf, T, k, kx0, p, nullptr);
+        __syncthreads();
+        const C* res = run_fft<R, NY, -1>(buf, p.tw_cols, p.bs_col, p.fy, ctab<R>(p.twy));
+        store_cols<R>(S, res, k, kx0, p);
+    }
 }
 
 // ---------------------------------------------------------------------------
-// a3: vertical tridiagonal problem per (kx, ky), one thread per column, FP64.
+// a3: vertical tridiagonal problem per (kx, ky), one thread per column.
 // Symmetric form (rows multiplied by rho_c dz):
-//   A[k] p[k-1] + b[k] p[k] + A[k+1] p[k+1] = D'[k],  b[k] = lambda s[k] - A[k] - A[k+1]
+//   A[k] p[k-1] + b[k] p[k] + A[k+1] p[k+1] = D'[k],  b[k] = lambda s[k] - (A[k] + A[k+1])
 // Forward: e = b - A^2/e_prev, y = D' - (A/e_prev) y_prev.  Back:
-// p[k] = (y[k] - A[k+1] p[k+1]) / e[k].  The (0,0) column pins p[0] = 0.
-// Writes p^ and the spectral w-gradient (p[k]-p[k-1])/dzn[k], both scaled
-// by 1/(nx ny) for the inverse transform.
+// p[k] = (y[k] - A[k+1] p[k+1]) / e[k].  The (0,0) column pins p[0] = 0 by
+// starting its elimination with y[0] = 0 and 1/e[0] = 0, which also decouples
+// level 0 from level 1.  Outputs p^ and the spectral w-gradient
+// (p[k]-p[k-1])/dzn[k], both scaled by 1/(nx ny) for the inverse transform.
+//
+// A warp takes 32 consecutive kx of one ky row.  Mixed plans run a warp in
+// FP32 unless its smallest |lambda| (at its first kx) is below lam_fp64, the
+// near-zero wavenumbers whose conditioning needs FP64; FP64 plans run every
+// column in FP64.  The forward sweep keeps y in S and 1/e in G (or, for FP64
+// columns of a mixed plan, y split over S and G and 1/e in Gp); the back
+// sweep reads them back and overwrites them with p^ and gz^.
 // ---------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(128) k_tridiag(ProjParams p) {
-    using C = cplx<R>;
-    const int ncol = p.ny * p.nxh;
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= ncol) return;
-    const int ky = col / p.nxh;
-    const int kx = col - ky * p.nxh;
-    const size_t LS = (size_t)p.ny * p.nxp;
-    const size_t base = (size_t)ky * p.nxp + kx;
+constexpr int kTriPrefetch = 8;
+
+template <typename T> struct VCoef;
+template <> struct VCoef<double> {
+    const double *a, *s, *c, *iz;
+    __device__ VCoef(const ProjParams& p) : a(p.acoef), s(p.svol), c(p.csum), iz(p.idzn) {}
+};
+template <> struct VCoef<float> {
+    const float *a, *s, *c, *iz;
+    __device__ VCoef(const ProjParams& p) : a(p.acoef32), s(p.svol32), c(p.csum32), iz(p.idzn32) {}
+};
+
+// Arithmetic and storage in the same precision T: y in S[k], 1/e in G[k].x.
+template <typename T>
+__device__ __forceinline__ void tridiag_column_inplace(const ProjParams& p, size_t base, T lam, bool mean) {
+    using C = cplx<T>;
     const int nz = p.nz;
+    const size_t LS = (size_t)p.ny * p.nxp;
     C* S = (C*)p.S;
     C* G = (C*)p.G;
+    const VCoef<T> vc(p);
+    const T scale = (T)p.scale;
+    T g = (T)0;
+    C y = cmk<T>((T)0, (T)0);
+    C cur[kTriPrefetch], nxt[kTriPrefetch];
+#pragma unroll
+    for (int i = 0; i < kTriPrefetch; ++i) cur[i] = (i < nz) ? S[i * LS + base] : cmk<T>((T)0, (T)0);
+    for (int kb = 0; kb < nz; kb += kTriPrefetch) {
+#pragma unroll
+        for (int i = 0; i < kTriPrefetch; ++i) {
+            const int k = kb + kTriPrefetch + i;
+            nxt[i] = (k < nz) ? S[k * LS + base] : cmk<T>((T)0, (T)0);
+        }
+#pragma unroll
+        for (int i = 0; i < kTriPrefetch; ++i) {
+            const int k = kb + i;
+            if (k < nz) {
+                const T ak = vc.a[k];
+                const T m = ak * g;
+                const T e = lam * vc.s[k] - vc.c[k] - ak * m;
+                T gk = (T)1 / e;
+                C yk = cmk<T>(cur[i].x - m * y.x, cur[i].y - m * y.y);
+                if (mean && k == 0) { gk = (T)0; yk = cmk<T>((T)0, (T)0); }
+                g = gk;
+                y = yk;
+                S[k * LS + base] = yk;
+                ((T*)&G[k * LS + base])[0] = gk;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kTriPrefetch; ++i) cur[i] = nxt[i];
+    }
+    // back substitution, top to bottom
+    C ph = cmk<T>(y.x * g, y.y * g);
+    S[(nz - 1) * LS + base] = cmk<T>(ph.x * scale, ph.y * scale);
+    C cy[kTriPrefetch], ny_[kTriPrefetch];
+    T cg[kTriPrefetch], ng[kTriPrefetch];
+#pragma unroll
+    for (int i = 0; i < kTriPrefetch; ++i) {
+        const int k = nz - 2 - i;
+        cy[i] = (k >= 0) ? S[k * LS + base] : cmk<T>((T)0, (T)0);
+        cg[i] = (k >= 0) ? ((const T*)&G[k * LS + base])[0] : (T)0;
+    }
+    for (int kb = nz - 2; kb >= 0; kb -= kTriPrefetch) {
+#pragma unroll
+        for (int i = 0; i < kTriPrefetch; ++i) {
+            const int k = kb - kTriPrefetch - i;
+            ny_[i] = (k >= 0) ? S[k * LS + base] : cmk<T>((T)0, (T)0);
+            ng[i] = (k >= 0) ? ((const T*)&G[k * LS + base])[0] : (T)0;
+        }
+#pragma unroll
+        for (int i = 0; i < kTriPrefetch; ++i) {
+            const int k = kb - i;
+            if (k >= 0) {
+                const T a1 = vc.a[k + 1];
+                const C pn = cmk<T>((cy[i].x - a1 * ph.x) * cg[i], (cy[i].y - a1 * ph.y) * cg[i]);
+                const T iz = vc.iz[k + 1] * scale;
+                G[(k + 1) * LS + base] = cmk<T>((ph.x - pn.x) * iz, (ph.y - pn.y) * iz);
+                S[k * LS + base] = cmk<T>(pn.x * scale, pn.y * scale);
+                ph = pn;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kTriPrefetch; ++i) { cy[i] = ny_[i]; cg[i] = ng[i]; }
+    }
+}
+
+// FP64 arithmetic on FP32 storage (near-zero wavenumbers of a mixed plan):
+// y.x in S[k] and y.y in G[k] (each slot reinterpreted as one double), 1/e in Gp.
+__device__ __forceinline__ void tridiag_column_mixed64(const ProjParams& p, size_t base, double lam, bool mean) {
+    const int nz = p.nz;
+    const size_t LS = (size_t)p.ny * p.nxp;
+    float2* S = (float2*)p.S;
+    float2* G = (float2*)p.G;
+    double* Sd = (double*)p.S;
+    double* Gd = (double*)p.G;
+    double* Gp = p.Gp;
+    const double scale = p.scale;
+    double g = 0.0;
+    double2 y = make_double2(0.0, 0.0);
+    for (int k = 0; k < nz; ++k) {
+        const size_t o = k * LS + base;
+        const float2 dv = S[o];
+        const double ak = p.acoef[k];
+        const double m = ak * g;
+        const double e = lam * p.svol[k] - p.csum[k] - ak * m;
+        double gk = 1.0 / e;
+        double2 yk = make_double2((double)dv.x - m * y.x, (double)dv.y - m * y.y);
+        if (mean && k == 0) { gk = 0.0; yk = make_double2(0.0, 0.0); }
+        g = gk;
+        y = yk;
+        Sd[o] = yk.x;
+        Gd[o] = yk.y;
+        Gp[o] = gk;
+    }
+    double2 ph = make_double2(y.x * g, y.y * g);
+    S[(nz - 1) * LS + base] = make_float2((float)(ph.x * scale), (float)(ph.y * scale));
+    for (int k = nz - 2; k >= 0; --k) {
+        const size_t o = k * LS + base;
+        const double yx = Sd[o], yy = Gd[o], gk = Gp[o];
+        const double a1 = p.acoef[k + 1];
+        const double2 pn = make_double2((yx - a1 * ph.x) * gk, (yy - a1 * ph.y) * gk);
+        const double iz = p.idzn[k + 1] * scale;
+        G[o + LS] = make_float2((float)((ph.x - pn.x) * iz), (float)((ph.y - pn.y) * iz));
+        S[o] = make_float2((float)(pn.x * scale), (float)(pn.y * scale));
+        ph = pn;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_tridiag(ProjParams p) {
+    const int nxw = (p.nxh + 31) & ~31;
+    const long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int ky = (int)(col / nxw);
+    const int kx = (int)(col - (long long)ky * nxw);
+    if (ky >= p.ny || kx >= p.nxh) return;
+    const size_t base = (size_t)ky * p.nxp + kx;
     const double lam = p.lamx[kx] + p.lamy[ky];
     const bool mean = (kx == 0 && ky == 0);
-    const int k0 = mean ? 1 : 0;
-    const double scale = p.scale;
-
-    if (k0 < nz) {
-        double g = 0.0;
-        double2 y = make_double2(0.0, 0.0);
-        for (int k = k0; k < nz; ++k) {
-            const double ak = (k > k0) ? p.acoef[k] : 0.0;
-            const double b = lam * p.svol[k] - p.acoef[k] - p.acoef[k + 1];
-            const double m = ak * g;
-            const double e = b - ak * m;
-            g = 1.0 / e;
-            C dv = S[k * LS + base];
-            y.x = (double)dv.x - m * y.x;
-            y.y = (double)dv.y - m * y.y;
-            p.Y[k * LS + base] = y;
-            p.Gp[k * LS + base] = g;
-        }
-        double2 ph = make_double2(y.x * g, y.y * g);
-        S[(nz - 1) * LS + base] = cmk<R>((R)(ph.x * scale), (R)(ph.y * scale));
-        for (int k = nz - 2; k >= k0; --k) {
-            const double a1 = p.acoef[k + 1];
-            const double2 yk = p.Y[k * LS + base];
-            const double gk = p.Gp[k * LS + base];
-            double2 pn = make_double2((yk.x - a1 * ph.x) * gk, (yk.y - a1 * ph.y) * gk);
-            const double iz = p.idzn[k + 1] * scale;
-            G[(k + 1) * LS + base] = cmk<R>((R)((ph.x - pn.x) * iz), (R)((ph.y - pn.y) * iz));
-            S[k * LS + base] = cmk<R>((R)(pn.x * scale), (R)(pn.y * scale));
-            ph = pn;
-        }
-        if (mean) {
-            // p[0] = 0 (the pin); face 1 gradient from p[1] - 0.
-            const double iz = p.idzn[1] * scale;
-            G[LS + base] = cmk<R>((R)(ph.x * iz), (R)(ph.y * iz));
-        }
+    if (sizeof(R) == 8) {
+        tridiag_column_inplace<double>(p, base, lam, mean);
+    } else {
+        const double lam_warp = p.lamx[kx & ~31] + p.lamy[ky];   // smallest |lambda| of the warp
+        if (-lam_warp < p.lam_fp64) tridiag_column_mixed64(p, base, lam, mean);
+        else tridiag_column_inplace<float>(p, base, (float)lam, mean);
     }
-    if (mean) S[base] = cmk<R>((R)0, (R)0);
 }
 
 // ---------------------------------------------------------------------------
 // a4 (y part): inverse y-transforms of one level's tile:
 //   Tp  = IFFT_y(p^),  Tgy = IFFT_y(p^ * ey),  Tgz = IFFT_y(gz^)  (gz^ not at k = 0)
 // ---------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(256) k_inv_cols(ProjParams p) {
+template <typename R, int NY>
+__global__ void __launch_bounds__(512) k_inv_cols(ProjParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using C = cplx<R>;
-    const int k = blockIdx.x / p.ntiles;
-    const int kx0 = (blockIdx.x - k * p.ntiles) * p.tw_cols;
-    C* bufA = (C*)smem_raw;
-    C* bufB = bufA + p.tw_cols * p.bs_col;
-    const C* ey = ctab<R>(p.ey);
-    for (int f = 0; f < 3; ++f) {
-        if (f == 2 && k == 0) break;
-        const C* src = (f == 2) ? (const C*)p.G : (const C*)p.S;
-        C* dst = (f == 0) ? (C*)p.Tp : (f == 1) ? (C*)p.Tgy : (C*)p.Tgz;
-        load_cols<R>(bufA, src, k, kx0, p, f == 1 ? ey : nullptr);
+    const int f = blockIdx.x % 3;
+    const int task = blockIdx.x / 3;
+    const int k = task / p.ntiles;
+    const int kx0 = (task - k * p.ntiles) * p.tw_cols;
+    if (f == 2 && k == 0) return;      // no w-gradient below the bottom face
+    C* buf = (C*)smem_raw;
+    const C* src = (f == 2) ? (const C*)p.G : (const C*)p.S;
+    C* dst = (f == 0) ? (C*)p.Tp : (f == 1) ? (C*)p.Tgy : (C*)p.Tgz;
+    const C* ey = (f == 1) ? ctab<R>(p.ey) : nullptr;
+    const int nxh = p.nxh, nxp = p.nxp, ny = p.ny;
+    if constexpr (NY > 0) {
+        auto load = [&](int c, int j) -> C {
+            const int kx = kx0 + c;
+            if (kx >= nxh) return cmk<R>((R)0, (R)0);
+            const C v = src[((size_t)k * ny + j) * nxp + kx];
+            return ey ? cmul(v, ey[j]) : v;
+        };
+        ct_first<R, NY, 1, true>(buf, p.tw_cols, p.bs_col, load);
+        CtMid<R, NY, StageInfo<R, NY, 1>::NEXT, 1>::run(buf, p.tw_cols, p.bs_col, ctab<R>(p.twy));
+        auto store = [&](int c, int q, const C* x, int ns) {
+            const int kx = kx0 + c;
+            if (kx >= nxh) return;
+            constexpr int RAD = StageInfo<R, NY, LastNs<R, NY>::value>::RAD;
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) dst[((size_t)k * ny + q + r * ns) * nxp + kx] = x[r];
+        };
+        ct_last<R, NY, 1, true>(buf, p.tw_cols, p.bs_col, ctab<R>(p.twy), store);
+    } else {
+        load_cols<R>(buf, src, k, kx0, p, ey);
         __syncthreads();
-        C* res = fft_batch<R, 1>(bufA, bufB, p.tw_cols, p.bs_col, p.fy, ctab<R>(p.twy));
+        const C* res = run_fft<R, NY, 1>(buf, p.tw_cols, p.bs_col, p.fy, ctab<R>(p.twy));
         store_cols<R>(dst, res, k, kx0, p);
-        __syncthreads();
     }
 }
 
@@ -278,8 +479,8 @@ __device__ __forceinline__ cplx<R> inv_spectrum(const ProjParams& p, int k, int 
     return val;
 }
 
-template <typename R>
-__global__ void __launch_bounds__(256) k_inv_rows(ProjParams p) {
+template <typename R, int NX>
+__global__ void __launch_bounds__(512) k_inv_rows(ProjParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using C = cplx<R>;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
@@ -291,21 +492,6 @@ __global__ void __launch_bounds__(256) k_inv_rows(ProjParams p) {
     const int np = nch * npr;                // complex transforms per task
     const int bs = p.bs_row;
     C* bufA = (C*)smem_raw;
-    C* bufB = bufA + np * bs;
-
-    const int tot = np * nx;
-    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-        const int q = t / nx;
-        const int kx = t - q * nx;
-        const int ch = q / npr;
-        const int m = q - ch * npr;
-        const int j = j0 + 2 * m;
-        C a = inv_spectrum<R>(p, k, j, ch, kx);
-        C b = inv_spectrum<R>(p, k, j + 1, ch, kx);
-        bufA[q * bs + kx] = cmk<R>(a.x - b.y, a.y + b.x);
-    }
-    __syncthreads();
-    C* res = fft_batch<R, 1>(bufA, bufB, np, bs, p.fx, ctab<R>(p.twx));
 
     const R* u = (const R*)p.u;
     const R* v = (const R*)p.v;
@@ -315,27 +501,125 @@ __global__ void __launch_bounds__(256) k_inv_rows(ProjParams p) {
     R* wo = (R*)p.wo;
     R* ph = (R*)p.phi;
     const size_t plane = (size_t)ny * nx;
-    const int tot2 = p.rows_inv * nx;
-    for (int t = threadIdx.x; t < tot2; t += blockDim.x) {
-        const int r = t / nx;
-        const int i = t - r * nx;
-        const int j = j0 + r;
-        if (j >= ny) continue;
-        const int m = r >> 1;
-        R val[4];
+    if constexpr (NX > 0) {
+        // compile-time length: the first stage reads the Hermitian-extended
+        // spectra straight from global memory; the last stage applies the
+        // correction of its channel (u, v, w or phi) straight to global memory
+        auto load = [&](int b, int kx) -> C {
+            const int ch = b / npr;
+            const int j = j0 + 2 * (b - ch * npr);
+            const C a = inv_spectrum<R>(p, k, j, ch, kx);
+            const C c = inv_spectrum<R>(p, k, j + 1, ch, kx);
+            return cmk<R>(a.x - c.y, a.y + c.x);
+        };
+        ct_first<R, NX, 1, false>(bufA, np, bs, load);
+        CtMid<R, NX, StageInfo<R, NX, 1>::NEXT, 1>::run(bufA, np, bs, ctab<R>(p.twx));
+        auto store = [&](int b, int q, const C* x, int ns) {
+            constexpr int RAD = StageInfo<R, NX, LastNs<R, NX>::value>::RAD;
+            const int ch = b / npr;
+            const int j = j0 + 2 * (b - ch * npr);
+            const R* in = (ch == 0) ? u : (ch == 1) ? v : w;
+            R* out = (ch == 0) ? uo : (ch == 1) ? vo : (ch == 2) ? wo : ph;
+            // per row: read every input first, then write (outputs may alias inputs)
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) {
-            if (ch < nch) {
-                const C z = res[(ch * npr + m) * bs + i];
-                val[ch] = (r & 1) ? z.y : z.x;
+            for (int h = 0; h < 2; ++h) {
+                if (j + h >= ny) continue;
+                const size_t row = (size_t)k * plane + (size_t)(j + h) * NX + q;
+                R prev[RAD];
+#pragma unroll
+                for (int r = 0; r < RAD; ++r)
+                    prev[r] = (ch < 3 && !(ch == 2 && k == 0)) ? in[row + r * ns] : (R)0;
+#pragma unroll
+                for (int r = 0; r < RAD; ++r) {
+                    const R val = h ? x[r].y : x[r].x;
+                    const size_t o = row + r * ns;
+                    if (ch == 3) out[o] = val;
+                    else if (ch == 2 && k == 0) out[o] = (R)0;
+                    else out[o] = prev[r] - val;
+                    if (ch == 2 && k == nz - 1) wo[o + plane] = (R)0;
+                }
+            }
+        };
+        ct_last<R, NX, 1, false>(bufA, np, bs, ctab<R>(p.twx), store);
+        return;
+    } else {
+        const int tot = np * nx;
+        const int step = kLoadBatch * blockDim.x;
+        for (int base = threadIdx.x; base < tot; base += step) {
+            C av[kLoadBatch], bv[kLoadBatch];
+#pragma unroll
+            for (int c = 0; c < kLoadBatch; ++c) {
+                const int t = base + c * blockDim.x;
+                av[c] = bv[c] = cmk<R>((R)0, (R)0);
+                if (t < tot) {
+                    const int q = (NX > 0) ? t / NX : t / nx;
+                    const int kx = t - q * nx;
+                    const int ch = q / npr;
+                    const int m = q - ch * npr;
+                    const int j = j0 + 2 * m;
+                    av[c] = inv_spectrum<R>(p, k, j, ch, kx);
+                    bv[c] = inv_spectrum<R>(p, k, j + 1, ch, kx);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < kLoadBatch; ++c) {
+                const int t = base + c * blockDim.x;
+                if (t < tot) {
+                    const int q = (NX > 0) ? t / NX : t / nx;
+                    const int kx = t - q * nx;
+                    bufA[q * bs + spad(kx)] = cmk<R>(av[c].x - bv[c].y, av[c].y + bv[c].x);
+                }
             }
         }
-        const size_t o = (size_t)k * plane + (size_t)j * nx + i;
-        uo[o] = u[o] - val[0];
-        vo[o] = v[o] - val[1];
-        wo[o] = (k == 0) ? (R)0 : (R)(w[o] - val[2]);
-        if (k == nz - 1) wo[o + plane] = (R)0;
-        if (nch == 4) ph[o] = val[3];
+        __syncthreads();
+        const C* res = run_fft<R, NX, 1>(bufA, np, bs, p.fx, ctab<R>(p.twx));
+
+        const int tot2 = p.rows_inv * nx;
+        const int step2 = kLoadBatch * blockDim.x;
+        for (int base = threadIdx.x; base < tot2; base += step2) {
+            R uu[kLoadBatch], vv[kLoadBatch], ww[kLoadBatch];
+#pragma unroll
+            for (int c = 0; c < kLoadBatch; ++c) {
+                const int t = base + c * blockDim.x;
+                uu[c] = vv[c] = ww[c] = (R)0;
+                if (t < tot2) {
+                    const int r = (NX > 0) ? t / NX : t / nx;
+                    const int i = t - r * nx;
+                    const int j = j0 + r;
+                    if (j < ny) {
+                        const size_t o = (size_t)k * plane + (size_t)j * nx + i;
+                        uu[c] = u[o];
+                        vv[c] = v[o];
+                        if (k > 0) ww[c] = w[o];
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < kLoadBatch; ++c) {
+                const int t = base + c * blockDim.x;
+                if (t >= tot2) continue;
+                const int r = (NX > 0) ? t / NX : t / nx;
+                const int i = t - r * nx;
+                const int j = j0 + r;
+                if (j >= ny) continue;
+                const int m = r >> 1;
+                R val[4];
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch) {
+                    if (ch < nch) {
+                        const C z = res[(ch * npr + m) * bs + spad(i)];
+                        val[ch] = (r & 1) ? z.y : z.x;
+                    }
+                }
+                const size_t o = (size_t)k * plane + (size_t)j * nx + i;
+                uo[o] = uu[c] - val[0];
+                vo[o] = vv[c] - val[1];
+                wo[o] = (k == 0) ? (R)0 : (R)(ww[c] - val[2]);
+                if (k == nz - 1) wo[o + plane] = (R)0;
+                if (nch == 4) ph[o] = val[3];
+            }
+        }
+
     }
 }
 

@@ -25,14 +25,19 @@ struct monc_proj_plan_s {
     void* dev_tables;
     const void* twx; const void* twy;
     const double* svol; const double* rflo; const double* rfhi;
-    const double* acoef; const double* idzn;
+    const double* acoef; const double* idzn; const double* csum;
+    const float* svol32; const float* acoef32; const float* csum32; const float* idzn32;
+    double lam_fp64;
+    long long fp64_cols;
     const double* lamx; const double* lamy;
     const void* ex; const void* ey;
     int* err;
     // task shapes
     int rows_fwd, nrb_fwd, tw_cols, ntiles;
+    int thr_fwd_rows, thr_cols;
+    int rows_inv[2], thr_inv_rows[2];
     int bs_row, bs_col;
-    size_t smem_fwd_rows, smem_cols;
+    size_t smem_fwd_rows, smem_cols, smem_inv_rows[2];
     // workspace layout
     size_t ws_bytes;
     size_t off_S, off_G, off_T, off_Tp, off_Tgy, off_Tgz, off_Y, off_Gp;
@@ -44,7 +49,6 @@ struct monc_proj_plan_s {
 
 namespace {
 
-constexpr int kThreads = 256;
 constexpr int kPhases = 5;
 const char* const kPhaseNames[kPhases] = {"fwd_rows", "fwd_cols", "tridiag", "inv_cols", "inv_rows"};
 
@@ -67,8 +71,12 @@ PhaseMarks begin_marks(monc_proj_plan_s* p) {
     p->nprof++;
     return m;
 }
-constexpr size_t kSmemRowBudget = 96 * 1024;
 constexpr size_t kSmemMax = 200 * 1024;
+// Mixed plans: a3 runs in FP64 for columns with |lambda| < kFp64Fraction * v_max.
+// The FP32 sweep's contribution to the divergence residual was measured (in an
+// FP32 emulation of the sweep) at about 7e-8 above this bound and grows to
+// 2e-7..5e-7 when the lowest wavenumbers are included.
+constexpr double kFp64Fraction = 0.02;
 
 bool is_smooth(int n) {
     if (n < 1) return false;
@@ -77,21 +85,45 @@ bool is_smooth(int n) {
     return n == 1;
 }
 
-FftFactors factorize(int n) {
+FastDiv make_fastdiv(unsigned d) {
+    unsigned sh = 0;
+    while ((1u << sh) < d) ++sh;
+    const unsigned long long m = ((1ull << 32) * ((1ull << sh) - d)) / d + 1;
+    return FastDiv{(unsigned)m, sh};
+}
+
+// Stockham radix plan, largest radices first (32 at most in FP32, 16 in FP64
+// where a 32-point register DFT would not fit the register file).
+FftFactors factorize(int n, int maxrad) {
     FftFactors f{};
     f.n = n;
-    int m = n;
-    int s = 0;
-    while (m % 8 == 0) { f.radix[s++] = 8; m /= 8; }
-    while (m % 4 == 0) { f.radix[s++] = 4; m /= 4; }
-    while (m % 2 == 0) { f.radix[s++] = 2; m /= 2; }
-    while (m % 5 == 0) { f.radix[s++] = 5; m /= 5; }
-    while (m % 3 == 0) { f.radix[s++] = 3; m /= 3; }
+    int m = n, s = 0, ns = 1;
+    auto push = [&](int r) {
+        FftStage& st = f.st[s++];
+        st.radix = r;
+        st.ns = ns;
+        st.nq = n / r;
+        st.fq = make_fastdiv((unsigned)st.nq);
+        st.fns = make_fastdiv((unsigned)ns);
+        ns *= r;
+        m /= r;
+    };
+    for (int r : {32, 16, 8, 4, 2})
+        while (r <= maxrad && m % r == 0) push(r);
+    while (m % 5 == 0) push(5);
+    while (m % 3 == 0) push(3);
     f.nstages = s;
     return f;
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Block size for a batch of `elems` transform elements at E per thread.
+int threads_for(int elems, int E) {
+    int t = (elems + E - 1) / E;
+    t = (t + 31) & ~31;
+    return std::max(32, std::min(512, t));
+}
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
@@ -143,6 +175,14 @@ void push_doubles(std::vector<unsigned char>& blob, const std::vector<double>& x
     blob.insert(blob.end(), b, b + x.size() * sizeof(double));
 }
 
+void push_floats(std::vector<unsigned char>& blob, const std::vector<double>& x) {
+    for (double v : x) {
+        const float f = (float)v;
+        const unsigned char* b = (const unsigned char*)&f;
+        blob.insert(blob.end(), b, b + sizeof(float));
+    }
+}
+
 void pad_blob(std::vector<unsigned char>& blob) {
     while (blob.size() % 256) blob.push_back(0);
 }
@@ -154,6 +194,8 @@ ProjParams make_params(const monc_proj_plan_s* p, const void* u, const void* v, 
     q.fx = p->fx; q.fy = p->fy;
     q.twx = p->twx; q.twy = p->twy;
     q.svol = p->svol; q.rflo = p->rflo; q.rfhi = p->rfhi; q.acoef = p->acoef; q.idzn = p->idzn;
+    q.csum = p->csum; q.svol32 = p->svol32; q.acoef32 = p->acoef32; q.csum32 = p->csum32;
+    q.idzn32 = p->idzn32; q.lam_fp64 = p->lam_fp64;
     q.lamx = p->lamx; q.lamy = p->lamy; q.ex = p->ex; q.ey = p->ey;
     q.idx = 1.0 / p->dx; q.idy = 1.0 / p->dy;
     q.scale = 1.0 / ((double)p->nx * (double)p->ny);
@@ -167,48 +209,102 @@ ProjParams make_params(const monc_proj_plan_s* p, const void* u, const void* v, 
     q.tw_cols = p->tw_cols; q.ntiles = p->ntiles;
     q.bs_row = p->bs_row; q.bs_col = p->bs_col;
     q.nch = phi ? 4 : 3;
-    // inverse row tasks: an even number of rows, chosen so that the packed
-    // transforms (one per channel and row pair) fit the forward tasks' budget
-    const int npair = std::max(1, p->rows_fwd / 2);
-    const int pairs = std::max(1, npair / q.nch);
-    q.rows_inv = 2 * pairs;
+    q.rows_inv = p->rows_inv[q.nch == 4 ? 1 : 0];
     q.nrb_inv = (p->ny + q.rows_inv - 1) / q.rows_inv;
     return q;
 }
 
+// ---------------------------------------------------------------------------
+// Kernel selection: lengths with a compile-time FFT plan get their own
+// instantiation; every other 2^a 3^b 5^c length runs the run-time plan.
+// ---------------------------------------------------------------------------
+using KernelFn = void (*)(ProjParams);
+
+bool ct_length(int n, bool fp64) {
+    if (fp64) return n == 64 || n == 128 || n == 256 || n == 1024;
+    return n == 64 || n == 96 || n == 128 || n == 192 || n == 256 || n == 512 || n == 1024;
+}
+
+
+#define MP_KERNEL_PICKER(NAME)                                                              \
+    template <typename R> KernelFn pick_##NAME(int n) {                                     \
+        if constexpr (sizeof(R) == 8) {                                                     \
+            switch (n) {                                                                    \
+                case 64: return NAME<R, 64>;                                                \
+                case 128: return NAME<R, 128>;                                              \
+                case 256: return NAME<R, 256>;                                              \
+                case 1024: return NAME<R, 1024>;                                            \
+                default: return NAME<R, 0>;                                                 \
+            }                                                                               \
+        } else {                                                                            \
+            switch (n) {                                                                    \
+                case 64: return NAME<R, 64>;                                                \
+                case 96: return NAME<R, 96>;                                                \
+                case 128: return NAME<R, 128>;                                              \
+                case 192: return NAME<R, 192>;                                              \
+                case 256: return NAME<R, 256>;                                              \
+                case 512: return NAME<R, 512>;                                              \
+                case 1024: return NAME<R, 1024>;                                            \
+                default: return NAME<R, 0>;                                                 \
+            }                                                                               \
+        }                                                                                   \
+    }
+MP_KERNEL_PICKER(k_fwd_rows)
+MP_KERNEL_PICKER(k_fwd_cols)
+MP_KERNEL_PICKER(k_inv_cols)
+MP_KERNEL_PICKER(k_inv_rows)
+#undef MP_KERNEL_PICKER
+
+struct SolveKernels {
+    KernelFn fwd_rows, fwd_cols, inv_cols, inv_rows;
+};
+
+template <typename R> SolveKernels pick_kernels(int nx, int ny) {
+    return SolveKernels{pick_k_fwd_rows<R>(nx), pick_k_fwd_cols<R>(ny), pick_k_inv_cols<R>(ny),
+                        pick_k_inv_rows<R>(nx)};
+}
+
 template <typename R>
 int launch_solve(monc_proj_plan_s* p, const ProjParams& q, cudaStream_t st) {
-    using C = cplx<R>;
     const int nz = p->nz;
-    const size_t smem_rows = p->smem_fwd_rows;
-    const size_t smem_cols = p->smem_cols;
-    const int np_inv = q.nch * (q.rows_inv / 2);
-    const size_t smem_inv_rows = (size_t)2 * np_inv * p->bs_row * sizeof(C);
-    static bool attr_set[2] = {false, false};
-    const int ai = sizeof(R) == 8 ? 0 : 1;
-    if (!attr_set[ai]) {
-        cudaFuncSetAttribute(k_fwd_rows<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
-        cudaFuncSetAttribute(k_fwd_cols<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
-        cudaFuncSetAttribute(k_inv_cols<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
-        cudaFuncSetAttribute(k_inv_rows<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
-        attr_set[ai] = true;
-    }
-    if (smem_rows > kSmemMax || smem_cols > kSmemMax || smem_inv_rows > kSmemMax) return MONC_PROJ_EUNSUPPORTED;
+    const SolveKernels ks = pick_kernels<R>(p->nx, p->ny);
+    const int inv_idx = (q.nch == 4) ? 1 : 0;
     const PhaseMarks pm = begin_marks(p);
     pm.mark(0, st);
-    k_fwd_rows<R><<<nz * p->nrb_fwd, kThreads, smem_rows, st>>>(q);
+    ks.fwd_rows<<<nz * p->nrb_fwd, p->thr_fwd_rows, p->smem_fwd_rows, st>>>(q);
     pm.mark(1, st);
-    k_fwd_cols<R><<<nz * p->ntiles, kThreads, smem_cols, st>>>(q);
+    ks.fwd_cols<<<nz * p->ntiles, p->thr_cols, p->smem_cols, st>>>(q);
     pm.mark(2, st);
-    const int ncol = p->ny * p->nxh;
-    k_tridiag<R><<<(ncol + 127) / 128, 128, 0, st>>>(q);
+    const long long ncol = (long long)p->ny * ((p->nxh + 31) & ~31);
+    k_tridiag<R><<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(q);
     pm.mark(3, st);
-    k_inv_cols<R><<<nz * p->ntiles, kThreads, smem_cols, st>>>(q);
+    ks.inv_cols<<<nz * p->ntiles * 3, p->thr_cols, p->smem_cols, st>>>(q);
     pm.mark(4, st);
-    k_inv_rows<R><<<nz * q.nrb_inv, kThreads, smem_inv_rows, st>>>(q);
+    ks.inv_rows<<<nz * q.nrb_inv, p->thr_inv_rows[inv_idx], p->smem_inv_rows[inv_idx], st>>>(q);
     pm.mark(5, st);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MONC_PROJ_OK : MONC_PROJ_ECUDA;
+}
+
+// Raise the dynamic shared-memory limit of the kernels a plan uses; fails if
+// the plan's blocks need more than the device allows.
+template <typename R>
+int set_kernel_attrs(const monc_proj_plan_s* p) {
+    const size_t need = std::max({p->smem_fwd_rows, p->smem_cols, p->smem_inv_rows[0], p->smem_inv_rows[1]});
+    if (need > kSmemMax) return MONC_PROJ_EUNSUPPORTED;
+    const SolveKernels ks = pick_kernels<R>(p->nx, p->ny);
+    const KernelFn fns[] = {ks.fwd_rows, ks.fwd_cols, ks.inv_cols, ks.inv_rows};
+    for (KernelFn f : fns)
+        if (cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return MONC_PROJ_ECUDA;
+        }
+    return MONC_PROJ_OK;
+}
+
+int plan_kernel_attrs(const monc_proj_plan_s* p) {
+    return p->precision == MONC_PROJ_FP64 ? set_kernel_attrs<double>(p) : set_kernel_attrs<float>(p);
 }
 
 // Argument checks shared by every entry point that takes grid arguments.
@@ -229,7 +325,7 @@ int validate_grid(int nx, int ny, int nz, double dx, double dy, const double* dz
 
 // Offsets of the plan's device tables inside one contiguous blob.
 struct TableOffsets {
-    size_t twx, twy, sv, rl, rh, a, iz, lx, ly, ex, ey, err;
+    size_t twx, twy, sv, rl, rh, a, iz, cs, sv32, a32, cs32, iz32, lx, ly, ex, ey, err;
 };
 
 // Fill the host-side part of a plan (sizes, radix plans, task shapes,
@@ -240,8 +336,8 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     p->nx = nx; p->ny = ny; p->nz = nz; p->dx = dx; p->dy = dy; p->precision = precision;
     p->nxh = nx / 2 + 1;
     p->nxp = (p->nxh + 3) & ~3;
-    p->fx = factorize(nx);
-    p->fy = factorize(ny);
+    p->fx = factorize(nx, precision == MONC_PROJ_FP64 ? 16 : 32);
+    p->fy = factorize(ny, precision == MONC_PROJ_FP64 ? 16 : 32);
 
     const bool fp64 = precision == MONC_PROJ_FP64;
     const size_t csz = fp64 ? 16 : 8;
@@ -261,25 +357,63 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
         rfhi[k] = (k < nz - 1) ? rho_f[k + 1] : 0.0;
     }
     for (int k = 1; k < nz; ++k) { acoef[k] = rho_f[k] / dzn[k]; idzn[k] = 1.0 / dzn[k]; }
+    std::vector<double> csum(nz);
+    for (int k = 0; k < nz; ++k) csum[k] = acoef[k] + acoef[k + 1];
     std::vector<double> lamx(p->nxh), lamy(ny);
     for (int m = 0; m < p->nxh; ++m) lamx[m] = -4.0 * sin_half_sq(m, nx) / (dx * dx);
     for (int m = 0; m < ny; ++m) lamy[m] = -4.0 * sin_half_sq(m, ny) / (dy * dy);
+    // a3 precision split (mixed plans): columns whose |lambda| is below
+    // kFp64Fraction of the largest vertical eigenvalue bound
+    // v_max = max_k 2 (A[k] + A[k+1]) / (rho_c dz)[k] run in FP64.
+    double vmax = 0.0;
+    for (int k = 0; k < nz; ++k) vmax = std::max(vmax, 2.0 * (acoef[k] + acoef[k + 1]) / svol[k]);
+    p->lam_fp64 = (precision == MONC_PROJ_FP64) ? INFINITY : kFp64Fraction * vmax;
+    {
+        const int nxw = (p->nxh + 31) & ~31;
+        long long n64 = 0;
+        for (int ky = 0; ky < ny; ++ky)
+            for (int kx0 = 0; kx0 < p->nxh; kx0 += 32)
+                if (-(lamx[kx0] + lamy[ky]) < p->lam_fp64) n64 += std::min(32, p->nxh - kx0);
+        (void)nxw;
+        p->fp64_cols = n64;
+    }
     // (exp(+2 pi i m/n) - 1)/d = (-2 sin^2(pi m/n) + i sin(2 pi m/n)) / d
     std::vector<double> exr(p->nxh), exi(p->nxh), eyr(ny), eyi(ny);
     for (int m = 0; m < p->nxh; ++m) { exr[m] = -2.0 * sin_half_sq(m, nx) / dx; exi[m] = -sx[m] / dx; }
     for (int m = 0; m < ny; ++m) { eyr[m] = -2.0 * sin_half_sq(m, ny) / dy; eyi[m] = -sy[m] / dy; }
 
+    // per-stage twiddle tables of the x and y plans: stage s owns entries
+    // [s*n, s*n + R*Ns), entry r*Ns + k = exp(-2 pi i r k / (Ns R))
+    auto stage_tables = [](const FftFactors& f, std::vector<double>& re, std::vector<double>& im) {
+        const int n = f.n;
+        re.assign((size_t)std::max(1, f.nstages) * n, 0.0);
+        im.assign(re.size(), 0.0);
+        for (int s = 0; s < f.nstages; ++s) {
+            const int R = f.st[s].radix, ns = f.st[s].ns;
+            for (int r = 0; r < R; ++r)
+                for (int k = 0; k < ns; ++k)
+                    twiddle(r * k, ns * R, &re[(size_t)s * n + r * ns + k], &im[(size_t)s * n + r * ns + k]);
+        }
+    };
+    std::vector<double> tsxr, tsxi, tsyr, tsyi;
+    stage_tables(p->fx, tsxr, tsxi);
+    stage_tables(p->fy, tsyr, tsyi);
     to.twx = blob.size();
-    if (fp64) push_complex<double>(blob, cx, sx); else push_complex<float>(blob, cx, sx);
+    if (fp64) push_complex<double>(blob, tsxr, tsxi); else push_complex<float>(blob, tsxr, tsxi);
     pad_blob(blob);
     to.twy = blob.size();
-    if (fp64) push_complex<double>(blob, cy, sy); else push_complex<float>(blob, cy, sy);
+    if (fp64) push_complex<double>(blob, tsyr, tsyi); else push_complex<float>(blob, tsyr, tsyi);
     pad_blob(blob);
     to.sv = blob.size(); push_doubles(blob, svol); pad_blob(blob);
     to.rl = blob.size(); push_doubles(blob, rflo); pad_blob(blob);
     to.rh = blob.size(); push_doubles(blob, rfhi); pad_blob(blob);
     to.a = blob.size(); push_doubles(blob, acoef); pad_blob(blob);
     to.iz = blob.size(); push_doubles(blob, idzn); pad_blob(blob);
+    to.cs = blob.size(); push_doubles(blob, csum); pad_blob(blob);
+    to.sv32 = blob.size(); push_floats(blob, svol); pad_blob(blob);
+    to.a32 = blob.size(); push_floats(blob, acoef); pad_blob(blob);
+    to.cs32 = blob.size(); push_floats(blob, csum); pad_blob(blob);
+    to.iz32 = blob.size(); push_floats(blob, idzn); pad_blob(blob);
     to.lx = blob.size(); push_doubles(blob, lamx); pad_blob(blob);
     to.ly = blob.size(); push_doubles(blob, lamy); pad_blob(blob);
     to.ex = blob.size();
@@ -291,20 +425,42 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     to.err = blob.size();
     blob.resize(blob.size() + 256, 0);
 
-    // ---- task shapes
-    p->bs_row = nx;
-    p->bs_col = ny + 1;
-    int npair = (int)std::max<size_t>(1, kSmemRowBudget / (2 * (size_t)nx * csz));
-    npair = std::min(npair, 8);
+    // ---- task shapes.  Compile-time lengths: one shared buffer, blocks of
+    // about 256 threads x E elements (E = 32 FP32, 16 FP64 values per thread).
+    // Run-time lengths: two buffers (ping-pong) within ~96 KB, 256 threads.
+    const int E = fp64 ? 16 : 32;
+    const bool ctx = ct_length(nx, fp64), cty = ct_length(ny, fp64);
+    p->bs_row = spad_len(nx);
+    // column tiles: a pitch of 4 (mod 16) complex elements spreads the
+    // columns of a tile over distinct shared-memory banks
+    p->bs_col = spad_len(ny);
+    while (p->bs_col % 16 != 4) ++p->bs_col;
+    const size_t budget = 96 * 1024;
+    int npair = ctx ? std::max(1, std::min(16, 256 * E / nx))
+                    : (int)std::max<size_t>(1, std::min<size_t>(8, budget / (2 * (size_t)p->bs_row * csz)));
     npair = std::min(npair, (ny + 1) / 2);
     p->rows_fwd = 2 * npair;
     p->nrb_fwd = (ny + p->rows_fwd - 1) / p->rows_fwd;
-    int tw = (int)std::max<size_t>(1, kSmemRowBudget / (2 * (size_t)(ny + 1) * csz));
-    tw = std::min(tw, fp64 ? 4 : 8);
+    p->thr_fwd_rows = ctx ? threads_for(npair * nx, E) : 256;
+    p->smem_fwd_rows = (size_t)(ctx ? 1 : 2) * npair * p->bs_row * csz;
+    int tw = cty ? std::max(1, std::min(32, 256 * E / ny))
+                 : (int)std::max<size_t>(1, std::min<size_t>(8, budget / (2 * (size_t)p->bs_col * csz)));
+    tw = std::min(tw, p->nxh);
     p->tw_cols = tw;
     p->ntiles = (p->nxh + tw - 1) / tw;
-    p->smem_fwd_rows = (size_t)2 * npair * p->bs_row * csz;
-    p->smem_cols = (size_t)2 * tw * p->bs_col * csz;
+    p->thr_cols = cty ? threads_for(tw * ny, E) : 256;
+    p->smem_cols = (size_t)(cty ? 1 : 2) * tw * p->bs_col * csz;
+    // inverse row tasks: pairs of rows, one complex transform per channel and
+    // row pair; index 0 without phi output (3 channels), 1 with (4 channels)
+    for (int idx = 0; idx < 2; ++idx) {
+        const int nch = 3 + idx;
+        int pairs = std::max(1, npair / nch);
+        pairs = std::min(pairs, (ny + 1) / 2);
+        const int np = nch * pairs;
+        p->rows_inv[idx] = 2 * pairs;
+        p->thr_inv_rows[idx] = ctx ? threads_for(np * nx, E) : 256;
+        p->smem_inv_rows[idx] = (size_t)(ctx ? 1 : 2) * np * p->bs_row * csz;
+    }
 
     // ---- workspace layout
     const size_t L = (size_t)nz * ny * p->nxp;
@@ -315,8 +471,8 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     p->off_Tp = off; off = align256(off + L * csz);
     p->off_Tgy = off; off = align256(off + L * csz);
     p->off_Tgz = off; off = align256(off + L * csz);
-    p->off_Y = off; off = align256(off + L * 16);
-    p->off_Gp = off; off = align256(off + L * 8);
+    p->off_Y = off;                                   // (unused)
+    p->off_Gp = off; if (!fp64) off = align256(off + L * 8);   // 1/e of FP64 columns (mixed)
     p->ws_bytes = off;
 }
 
@@ -326,6 +482,9 @@ void plan_bind(monc_proj_plan_s* p, unsigned char* db, const TableOffsets& to) {
     p->svol = (const double*)(db + to.sv); p->rflo = (const double*)(db + to.rl);
     p->rfhi = (const double*)(db + to.rh); p->acoef = (const double*)(db + to.a);
     p->idzn = (const double*)(db + to.iz); p->lamx = (const double*)(db + to.lx);
+    p->csum = (const double*)(db + to.cs);
+    p->svol32 = (const float*)(db + to.sv32); p->acoef32 = (const float*)(db + to.a32);
+    p->csum32 = (const float*)(db + to.cs32); p->idzn32 = (const float*)(db + to.iz32);
     p->lamy = (const double*)(db + to.ly); p->ex = db + to.ex; p->ey = db + to.ey;
     p->err = (int*)(db + to.err);
 }
@@ -362,6 +521,8 @@ int monc_proj_plan(monc_proj_plan_t* out, int nx, int ny, int nz, double dx, dou
     TableOffsets to{};
     plan_prepare(p, nx, ny, nz, dx, dy, dz, rho_c, rho_f, precision, blob, to);
     cudaGetDevice(&p->device);
+    const int ar = plan_kernel_attrs(p);
+    if (ar != MONC_PROJ_OK) { delete p; return ar; }
 
     void* d = nullptr;
     if (cudaMalloc(&d, blob.size()) != cudaSuccess) { cudaGetLastError(); delete p; return MONC_PROJ_ENOMEM; }
@@ -491,7 +652,7 @@ int monc_proj_plan_info(monc_proj_plan_t plan, int* nx, int* ny, int* nz, int* p
     if (precision) *precision = plan->precision;
     const long long tot = (long long)plan->ny * plan->nxh;
     if (total_columns) *total_columns = tot;
-    if (fp64_columns) *fp64_columns = tot;
+    if (fp64_columns) *fp64_columns = plan->fp64_cols;
     return MONC_PROJ_OK;
 }
 
@@ -551,6 +712,8 @@ extern "C" int monc_proj_solve_noalloc(int nx, int ny, int nz, double dx, double
     void* base = nullptr;
     const int br = noalloc_base(&base, &plan.device);
     if (br != MONC_PROJ_OK) return br;
+    const int ar = plan_kernel_attrs(&plan);
+    if (ar != MONC_PROJ_OK) return ar;
     cudaStream_t st = (cudaStream_t)stream;
     // The blob carries a zeroed device error word, so every call starts clean.
     if (cudaMemcpyAsync(base, blob.data(), blob.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) {
