@@ -4,7 +4,7 @@
 // pressure-gradient correction (step a5) fused into the inverse transform.
 //
 // Layouts (element = one complex value of the storage precision R):
-//   spectral arrays  S, G, T, Tp, Tgy, Tgz : [nz][ny][nxp], kx < nxh valid
+//   spectral arrays  S, G, T, Tp, Tgy, Tgz, Tphi : [nz][ny][nxp], kx < nxh valid
 //   u, v, phi        : [nz][ny][nx] real;   w : [nz+1][ny][nx] real
 #pragma once
 #include "fft.cuh"
@@ -37,7 +37,7 @@ struct ProjParams {
     const void* u; const void* v; const void* w;
     void* uo; void* vo; void* wo; void* phi;
     // workspace
-    void* S; void* G; void* T; void* Tp; void* Tgy; void* Tgz;
+    void* S; void* G; void* T; void* Tp; void* Tgy; void* Tgz; void* Tphi;
     double2* Y; double* Gp;
     int* err;
     // task shapes
@@ -411,53 +411,66 @@ __global__ void __launch_bounds__(128) k_tridiag(ProjParams p) {
 }
 
 // ---------------------------------------------------------------------------
-// a4 (y part): inverse y-transforms of one level's tile:
-//   Tp  = IFFT_y(p^),  Tgy = IFFT_y(p^ * ey),  Tgz = IFFT_y(gz^)  (gz^ not at k = 0)
+// a4 (y part): inverse y-transforms of one level's tile, one field per task:
+//   f = 0: Tp   = IFFT_y(p^) * ex   (x-gradient; ex depends on the column only)
+//   f = 1: Tgy  = IFFT_y(p^ * ey)   (y-gradient)
+//   f = 2: Tgz  = IFFT_y(gz^)       (z-gradient; nothing at k = 0)
+//   f = 3: Tphi = IFFT_y(p^)        (only when phi is requested)
 // ---------------------------------------------------------------------------
+template <typename R>
+struct InvColField {
+    const cplx<R>* src;
+    cplx<R>* dst;
+    const cplx<R>* ey;      // non-null: multiply the input by ey[j]
+    bool ex;                // multiply the output by ex[kx]
+    bool skip;
+};
+template <typename R>
+__device__ __forceinline__ InvColField<R> inv_col_field(const ProjParams& p, int f, int k) {
+    using C = cplx<R>;
+    InvColField<R> r;
+    r.src = (f == 2) ? (const C*)p.G : (const C*)p.S;
+    r.dst = (f == 0) ? (C*)p.Tp : (f == 1) ? (C*)p.Tgy : (f == 2) ? (C*)p.Tgz : (C*)p.Tphi;
+    r.ey = (f == 1) ? ctab<R>(p.ey) : nullptr;
+    r.ex = (f == 0);
+    r.skip = (f == 2 && k == 0);
+    return r;
+}
+
 template <typename R, int NY>
 __global__ void __launch_bounds__(512) k_inv_cols(ProjParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using C = cplx<R>;
-    const int f = blockIdx.x % 3;
-    const int task = blockIdx.x / 3;
+    const int nf = p.nch;
+    const int f = blockIdx.x % nf;
+    const int task = blockIdx.x / nf;
     const int k = task / p.ntiles;
     const int kx0 = (task - k * p.ntiles) * p.tw_cols;
-    if (f == 2 && k == 0) return;      // no w-gradient below the bottom face
+    const InvColField<R> fd = inv_col_field<R>(p, f, k);
+    if (fd.skip) return;
     C* buf = (C*)smem_raw;
-    const C* src = (f == 2) ? (const C*)p.G : (const C*)p.S;
-    C* dst = (f == 0) ? (C*)p.Tp : (f == 1) ? (C*)p.Tgy : (C*)p.Tgz;
-    const C* ey = (f == 1) ? ctab<R>(p.ey) : nullptr;
-    const int nxh = p.nxh, nxp = p.nxp, ny = p.ny;
-    if constexpr (NY > 0) {
-        auto load = [&](int c, int j) -> C {
-            const int kx = kx0 + c;
-            if (kx >= nxh) return cmk<R>((R)0, (R)0);
-            const C v = src[((size_t)k * ny + j) * nxp + kx];
-            return ey ? cmul(v, ey[j]) : v;
-        };
-        ct_first<R, NY, 1, true>(buf, p.tw_cols, p.bs_col, load);
-        CtMid<R, NY, StageInfo<R, NY, 1>::NEXT, 1>::run(buf, p.tw_cols, p.bs_col, ctab<R>(p.twy));
-        auto store = [&](int c, int q, const C* x, int ns) {
-            const int kx = kx0 + c;
-            if (kx >= nxh) return;
-            constexpr int RAD = StageInfo<R, NY, LastNs<R, NY>::value>::RAD;
-#pragma unroll
-            for (int r = 0; r < RAD; ++r) dst[((size_t)k * ny + q + r * ns) * nxp + kx] = x[r];
-        };
-        ct_last<R, NY, 1, true>(buf, p.tw_cols, p.bs_col, ctab<R>(p.twy), store);
-    } else {
-        load_cols<R>(buf, src, k, kx0, p, ey);
+    load_cols<R>(buf, fd.src, k, kx0, p, fd.ey);
+    __syncthreads();
+    C* res = run_fft<R, NY, 1>(buf, p.tw_cols, p.bs_col, p.fy, ctab<R>(p.twy));
+    if (fd.ex) {
+        const C* ex = ctab<R>(p.ex);
+        const int tot = p.ny * p.tw_cols;
+        for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+            const int j = t / p.tw_cols;
+            const int c = t - j * p.tw_cols;
+            const int kx = min(kx0 + c, p.nxh - 1);
+            C* e = &res[c * p.bs_col + spad(j)];
+            *e = cmul(*e, ex[kx]);
+        }
         __syncthreads();
-        const C* res = run_fft<R, NY, 1>(buf, p.tw_cols, p.bs_col, p.fy, ctab<R>(p.twy));
-        store_cols<R>(dst, res, k, kx0, p);
     }
+    store_cols<R>(fd.dst, res, k, kx0, p);
 }
 
 // ---------------------------------------------------------------------------
-// a4 (x part) + a5: inverse real transforms along x of the gradient
-// channels of a block of rows, then u -= gx, v -= gy, w -= gz (w = 0 on the
-// bottom and top faces) and optionally phi.  Channels of a row:
-//   0: Tp * ex (x-gradient)   1: Tgy (y-gradient)   2: Tgz (z-gradient)   3: Tp (phi)
+// a4 (x part) + a5: inverse real transforms along x, then u -= gx, v -= gy,
+// w -= gz (w = 0 on the bottom and top faces) and optionally phi.  Channels:
+//   0: Tp (x-gradient)   1: Tgy (y-gradient)   2: Tgz (z-gradient)   3: Tphi (phi)
 // One complex transform carries one channel of two adjacent rows,
 // Z = A_j + i A_{j+1} with Hermitian-extended A; the real part of the inverse
 // is row j, the imaginary part row j+1.  Channels are never mixed in one
@@ -465,84 +478,104 @@ __global__ void __launch_bounds__(512) k_inv_cols(ProjParams p) {
 // its rounding error into a gradient channel.
 // ---------------------------------------------------------------------------
 template <typename R>
-__device__ __forceinline__ cplx<R> inv_spectrum(const ProjParams& p, int k, int j, int ch, int kx) {
+__device__ __forceinline__ const cplx<R>* inv_channel_spectrum(const ProjParams& p, int ch) {
     using C = cplx<R>;
-    if (j >= p.ny || (ch == 2 && k == 0)) return cmk<R>((R)0, (R)0);
-    const int nx = p.nx;
-    const bool neg = kx >= p.nxh;
+    return (ch == 0) ? (const C*)p.Tp : (ch == 1) ? (const C*)p.Tgy : (ch == 2) ? (const C*)p.Tgz : (const C*)p.Tphi;
+}
+
+// Hermitian-extended spectrum of one row at kx in [0, nx).
+template <typename R>
+__device__ __forceinline__ cplx<R> hermitian_at(const cplx<R>* row, int nx, int nxh, int kx) {
+    const bool neg = kx >= nxh;
     const int kk = neg ? nx - kx : kx;
-    const C* src = (ch == 1) ? (const C*)p.Tgy : (ch == 2) ? (const C*)p.Tgz : (const C*)p.Tp;
-    C val = src[((size_t)k * p.ny + j) * p.nxp + kk];
-    if (ch == 0) val = cmul(val, ctab<R>(p.ex)[kk]);
+    cplx<R> val = row[kk];
     if (kk == 0 || 2 * kk == nx) val.y = (R)0;      // real-only DC / Nyquist
     if (neg) val.y = -val.y;
     return val;
 }
 
+template <typename R>
+__device__ __forceinline__ cplx<R> inv_spectrum(const ProjParams& p, int k, int j, int ch, int kx) {
+    if (j >= p.ny || (ch == 2 && k == 0)) return cmk<R>((R)0, (R)0);
+    const cplx<R>* row = inv_channel_spectrum<R>(p, ch) + ((size_t)k * p.ny + j) * p.nxp;
+    return hermitian_at<R>(row, p.nx, p.nxh, kx);
+}
+
+// Compile-time lengths: one channel per task, task = (level, row block, channel).
+// Generic lengths: all channels of a row block in one task.
 template <typename R, int NX>
 __global__ void __launch_bounds__(512) k_inv_rows(ProjParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using C = cplx<R>;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const int nrb = p.nrb_inv;
-    const int k = blockIdx.x / nrb;
-    const int j0 = (blockIdx.x - k * nrb) * p.rows_inv;
     const int nch = p.nch;
-    const int npr = p.rows_inv / 2;          // row pairs per task
-    const int np = nch * npr;                // complex transforms per task
     const int bs = p.bs_row;
     C* bufA = (C*)smem_raw;
-
-    const R* u = (const R*)p.u;
-    const R* v = (const R*)p.v;
-    const R* w = (const R*)p.w;
-    R* uo = (R*)p.uo;
-    R* vo = (R*)p.vo;
-    R* wo = (R*)p.wo;
-    R* ph = (R*)p.phi;
     const size_t plane = (size_t)ny * nx;
     if constexpr (NX > 0) {
-        // compile-time length: the first stage reads the Hermitian-extended
-        // spectra straight from global memory; the last stage applies the
-        // correction of its channel (u, v, w or phi) straight to global memory
+        constexpr int NXH = NX / 2 + 1;
+        const int ch = blockIdx.x % nch;
+        const int t2 = blockIdx.x / nch;
+        const int k = t2 / nrb;
+        const int j0 = (t2 - k * nrb) * p.rows_inv;
+        const int npr = p.rows_inv / 2;              // transforms (row pairs) per task
+        R* out = (ch == 0) ? (R*)p.uo : (ch == 1) ? (R*)p.vo : (ch == 2) ? (R*)p.wo : (R*)p.phi;
+        if (ch == 2 && k == 0) {
+            // bottom face: w = 0
+            for (int t = threadIdx.x; t < p.rows_inv * NX; t += blockDim.x) {
+                const int j = j0 + t / NX;
+                if (j < ny) {
+                    out[(size_t)j * NX + (t % NX)] = (R)0;
+                    if (nz == 1) out[plane + (size_t)j * NX + (t % NX)] = (R)0;   // top face too
+                }
+            }
+            return;
+        }
+        const R* in = (ch == 0) ? (const R*)p.u : (ch == 1) ? (const R*)p.v : (const R*)p.w;
+        const C* spec = inv_channel_spectrum<R>(p, ch) + (size_t)k * ny * p.nxp;
+        const int nxp = p.nxp;
         auto load = [&](int b, int kx) -> C {
-            const int ch = b / npr;
-            const int j = j0 + 2 * (b - ch * npr);
-            const C a = inv_spectrum<R>(p, k, j, ch, kx);
-            const C c = inv_spectrum<R>(p, k, j + 1, ch, kx);
+            const int j = j0 + 2 * b;
+            C a = cmk<R>((R)0, (R)0), c = cmk<R>((R)0, (R)0);
+            if (j < ny) a = hermitian_at<R>(spec + (size_t)j * nxp, NX, NXH, kx);
+            if (j + 1 < ny) c = hermitian_at<R>(spec + (size_t)(j + 1) * nxp, NX, NXH, kx);
             return cmk<R>(a.x - c.y, a.y + c.x);
         };
-        ct_first<R, NX, 1, false>(bufA, np, bs, load);
-        CtMid<R, NX, StageInfo<R, NX, 1>::NEXT, 1>::run(bufA, np, bs, ctab<R>(p.twx));
+        ct_first<R, NX, 1, false>(bufA, npr, bs, load);
+        CtMid<R, NX, StageInfo<R, NX, 1>::NEXT, 1>::run(bufA, npr, bs, ctab<R>(p.twx));
         auto store = [&](int b, int q, const C* x, int ns) {
             constexpr int RAD = StageInfo<R, NX, LastNs<R, NX>::value>::RAD;
-            const int ch = b / npr;
-            const int j = j0 + 2 * (b - ch * npr);
-            const R* in = (ch == 0) ? u : (ch == 1) ? v : w;
-            R* out = (ch == 0) ? uo : (ch == 1) ? vo : (ch == 2) ? wo : ph;
-            // per row: read every input first, then write (outputs may alias inputs)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                if (j + h >= ny) continue;
-                const size_t row = (size_t)k * plane + (size_t)(j + h) * NX + q;
+                const int j = j0 + 2 * b + h;
+                if (j >= ny) continue;
+                const size_t row = (size_t)k * plane + (size_t)j * NX + q;
+                // read every input first, then write (outputs may alias inputs)
                 R prev[RAD];
 #pragma unroll
-                for (int r = 0; r < RAD; ++r)
-                    prev[r] = (ch < 3 && !(ch == 2 && k == 0)) ? in[row + r * ns] : (R)0;
+                for (int r = 0; r < RAD; ++r) prev[r] = (ch < 3) ? in[row + r * ns] : (R)0;
 #pragma unroll
                 for (int r = 0; r < RAD; ++r) {
                     const R val = h ? x[r].y : x[r].x;
-                    const size_t o = row + r * ns;
-                    if (ch == 3) out[o] = val;
-                    else if (ch == 2 && k == 0) out[o] = (R)0;
-                    else out[o] = prev[r] - val;
-                    if (ch == 2 && k == nz - 1) wo[o + plane] = (R)0;
+                    out[row + r * ns] = (ch < 3) ? prev[r] - val : val;
+                    if (ch == 2 && k == nz - 1) out[row + r * ns + plane] = (R)0;
                 }
             }
         };
-        ct_last<R, NX, 1, false>(bufA, np, bs, ctab<R>(p.twx), store);
-        return;
+        ct_last<R, NX, 1, false>(bufA, npr, bs, ctab<R>(p.twx), store);
     } else {
+        const int k = blockIdx.x / nrb;
+        const int j0 = (blockIdx.x - k * nrb) * p.rows_inv;
+        const int npr = p.rows_inv / 2;
+        const int np = nch * npr;
+        const R* u = (const R*)p.u;
+        const R* v = (const R*)p.v;
+        const R* w = (const R*)p.w;
+        R* uo = (R*)p.uo;
+        R* vo = (R*)p.vo;
+        R* wo = (R*)p.wo;
+        R* ph = (R*)p.phi;
         const int tot = np * nx;
         const int step = kLoadBatch * blockDim.x;
         for (int base = threadIdx.x; base < tot; base += step) {
@@ -552,7 +585,7 @@ __global__ void __launch_bounds__(512) k_inv_rows(ProjParams p) {
                 const int t = base + c * blockDim.x;
                 av[c] = bv[c] = cmk<R>((R)0, (R)0);
                 if (t < tot) {
-                    const int q = (NX > 0) ? t / NX : t / nx;
+                    const int q = t / nx;
                     const int kx = t - q * nx;
                     const int ch = q / npr;
                     const int m = q - ch * npr;
@@ -565,7 +598,7 @@ __global__ void __launch_bounds__(512) k_inv_rows(ProjParams p) {
             for (int c = 0; c < kLoadBatch; ++c) {
                 const int t = base + c * blockDim.x;
                 if (t < tot) {
-                    const int q = (NX > 0) ? t / NX : t / nx;
+                    const int q = t / nx;
                     const int kx = t - q * nx;
                     bufA[q * bs + spad(kx)] = cmk<R>(av[c].x - bv[c].y, av[c].y + bv[c].x);
                 }
@@ -573,7 +606,6 @@ __global__ void __launch_bounds__(512) k_inv_rows(ProjParams p) {
         }
         __syncthreads();
         const C* res = run_fft<R, NX, 1>(bufA, np, bs, p.fx, ctab<R>(p.twx));
-
         const int tot2 = p.rows_inv * nx;
         const int step2 = kLoadBatch * blockDim.x;
         for (int base = threadIdx.x; base < tot2; base += step2) {
@@ -583,7 +615,7 @@ __global__ void __launch_bounds__(512) k_inv_rows(ProjParams p) {
                 const int t = base + c * blockDim.x;
                 uu[c] = vv[c] = ww[c] = (R)0;
                 if (t < tot2) {
-                    const int r = (NX > 0) ? t / NX : t / nx;
+                    const int r = t / nx;
                     const int i = t - r * nx;
                     const int j = j0 + r;
                     if (j < ny) {
@@ -598,7 +630,7 @@ __global__ void __launch_bounds__(512) k_inv_rows(ProjParams p) {
             for (int c = 0; c < kLoadBatch; ++c) {
                 const int t = base + c * blockDim.x;
                 if (t >= tot2) continue;
-                const int r = (NX > 0) ? t / NX : t / nx;
+                const int r = t / nx;
                 const int i = t - r * nx;
                 const int j = j0 + r;
                 if (j >= ny) continue;
@@ -619,7 +651,6 @@ __global__ void __launch_bounds__(512) k_inv_rows(ProjParams p) {
                 if (nch == 4) ph[o] = val[3];
             }
         }
-
     }
 }
 

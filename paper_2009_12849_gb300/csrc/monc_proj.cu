@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "persist.cuh"
 
 using namespace mp;
 
@@ -36,11 +37,14 @@ struct monc_proj_plan_s {
     int rows_fwd, nrb_fwd, tw_cols, ntiles;
     int thr_fwd_rows, thr_cols;
     int rows_inv[2], thr_inv_rows[2];
+    int nsm;                              // SMs of the plan's device (persistent grids)
+    bool persist_cols;                    // compile-time lengths: persistent cp.async column kernels
+    bool ct_rows;                         // compile-time length along x
     int bs_row, bs_col;
     size_t smem_fwd_rows, smem_cols, smem_inv_rows[2];
     // workspace layout
     size_t ws_bytes;
-    size_t off_S, off_G, off_T, off_Tp, off_Tgy, off_Tgz, off_Y, off_Gp;
+    size_t off_S, off_G, off_T, off_Tp, off_Tgy, off_Tgz, off_Tphi, off_Y, off_Gp;
     // per-phase timing
     bool profiling;
     int nprof;
@@ -72,6 +76,7 @@ PhaseMarks begin_marks(monc_proj_plan_s* p) {
     return m;
 }
 constexpr size_t kSmemMax = 200 * 1024;
+constexpr size_t kSmemPersist = 220 * 1024;
 // Mixed plans: a3 runs in FP64 for columns with |lambda| < kFp64Fraction * v_max.
 // The FP32 sweep's contribution to the divergence residual was measured (in an
 // FP32 emulation of the sweep) at about 7e-8 above this bound and grows to
@@ -202,7 +207,7 @@ ProjParams make_params(const monc_proj_plan_s* p, const void* u, const void* v, 
     q.u = u; q.v = v; q.w = w; q.uo = uo; q.vo = vo; q.wo = wo; q.phi = phi;
     unsigned char* b = (unsigned char*)ws;
     q.S = b + p->off_S; q.G = b + p->off_G; q.T = b + p->off_T;
-    q.Tp = b + p->off_Tp; q.Tgy = b + p->off_Tgy; q.Tgz = b + p->off_Tgz;
+    q.Tp = b + p->off_Tp; q.Tgy = b + p->off_Tgy; q.Tgz = b + p->off_Tgz; q.Tphi = b + p->off_Tphi;
     q.Y = (double2*)(b + p->off_Y); q.Gp = (double*)(b + p->off_Gp);
     q.err = p->err;
     q.rows_fwd = p->rows_fwd; q.nrb_fwd = p->nrb_fwd;
@@ -255,32 +260,64 @@ MP_KERNEL_PICKER(k_inv_cols)
 MP_KERNEL_PICKER(k_inv_rows)
 #undef MP_KERNEL_PICKER
 
+#define MP_PERSIST_PICKER(NAME, KERNEL, ...)                                                \
+    template <typename R> KernelFn NAME(int n) {                                            \
+        if constexpr (sizeof(R) == 8) {                                                     \
+            switch (n) {                                                                    \
+                case 64: return KERNEL<R, 64 __VA_ARGS__>;                                  \
+                case 128: return KERNEL<R, 128 __VA_ARGS__>;                                \
+                case 256: return KERNEL<R, 256 __VA_ARGS__>;                                \
+                case 1024: return KERNEL<R, 1024 __VA_ARGS__>;                              \
+                default: return nullptr;                                                    \
+            }                                                                               \
+        } else {                                                                            \
+            switch (n) {                                                                    \
+                case 64: return KERNEL<R, 64 __VA_ARGS__>;                                  \
+                case 96: return KERNEL<R, 96 __VA_ARGS__>;                                  \
+                case 128: return KERNEL<R, 128 __VA_ARGS__>;                                \
+                case 192: return KERNEL<R, 192 __VA_ARGS__>;                                \
+                case 256: return KERNEL<R, 256 __VA_ARGS__>;                                \
+                case 512: return KERNEL<R, 512 __VA_ARGS__>;                                \
+                case 1024: return KERNEL<R, 1024 __VA_ARGS__>;                              \
+                default: return nullptr;                                                    \
+            }                                                                               \
+        }                                                                                   \
+    }
+MP_PERSIST_PICKER(pick_fwd_cols_persist, k_cols_persist, , false)
+MP_PERSIST_PICKER(pick_inv_cols_persist, k_cols_persist, , true)
+#undef MP_PERSIST_PICKER
+
 struct SolveKernels {
     KernelFn fwd_rows, fwd_cols, inv_cols, inv_rows;
 };
 
-template <typename R> SolveKernels pick_kernels(int nx, int ny) {
-    return SolveKernels{pick_k_fwd_rows<R>(nx), pick_k_fwd_cols<R>(ny), pick_k_inv_cols<R>(ny),
+template <typename R> SolveKernels pick_kernels(const monc_proj_plan_s* p) {
+    const int nx = p->nx, ny = p->ny;
+    return SolveKernels{pick_k_fwd_rows<R>(nx),
+                        p->persist_cols ? pick_fwd_cols_persist<R>(ny) : pick_k_fwd_cols<R>(ny),
+                        p->persist_cols ? pick_inv_cols_persist<R>(ny) : pick_k_inv_cols<R>(ny),
                         pick_k_inv_rows<R>(nx)};
 }
 
 template <typename R>
 int launch_solve(monc_proj_plan_s* p, const ProjParams& q, cudaStream_t st) {
     const int nz = p->nz;
-    const SolveKernels ks = pick_kernels<R>(p->nx, p->ny);
+    const SolveKernels ks = pick_kernels<R>(p);
     const int inv_idx = (q.nch == 4) ? 1 : 0;
+    const int n_fcols = nz * p->ntiles, n_icols = nz * p->ntiles * q.nch;
+    const int n_irows = nz * q.nrb_inv * (p->ct_rows ? q.nch : 1);
     const PhaseMarks pm = begin_marks(p);
     pm.mark(0, st);
     ks.fwd_rows<<<nz * p->nrb_fwd, p->thr_fwd_rows, p->smem_fwd_rows, st>>>(q);
     pm.mark(1, st);
-    ks.fwd_cols<<<nz * p->ntiles, p->thr_cols, p->smem_cols, st>>>(q);
+    ks.fwd_cols<<<p->persist_cols ? std::min(n_fcols, p->nsm) : n_fcols, p->thr_cols, p->smem_cols, st>>>(q);
     pm.mark(2, st);
     const long long ncol = (long long)p->ny * ((p->nxh + 31) & ~31);
     k_tridiag<R><<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(q);
     pm.mark(3, st);
-    ks.inv_cols<<<nz * p->ntiles * 3, p->thr_cols, p->smem_cols, st>>>(q);
+    ks.inv_cols<<<p->persist_cols ? std::min(n_icols, p->nsm) : n_icols, p->thr_cols, p->smem_cols, st>>>(q);
     pm.mark(4, st);
-    ks.inv_rows<<<nz * q.nrb_inv, p->thr_inv_rows[inv_idx], p->smem_inv_rows[inv_idx], st>>>(q);
+    ks.inv_rows<<<n_irows, p->thr_inv_rows[inv_idx], p->smem_inv_rows[inv_idx], st>>>(q);
     pm.mark(5, st);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MONC_PROJ_OK : MONC_PROJ_ECUDA;
@@ -290,12 +327,16 @@ int launch_solve(monc_proj_plan_s* p, const ProjParams& q, cudaStream_t st) {
 // the plan's blocks need more than the device allows.
 template <typename R>
 int set_kernel_attrs(const monc_proj_plan_s* p) {
-    const size_t need = std::max({p->smem_fwd_rows, p->smem_cols, p->smem_inv_rows[0], p->smem_inv_rows[1]});
-    if (need > kSmemMax) return MONC_PROJ_EUNSUPPORTED;
-    const SolveKernels ks = pick_kernels<R>(p->nx, p->ny);
+    const size_t lim_cols = p->persist_cols ? kSmemPersist : kSmemMax;
+    const size_t lim_rows = kSmemMax;
+    if (p->smem_fwd_rows > kSmemMax || p->smem_cols > lim_cols ||
+        std::max(p->smem_inv_rows[0], p->smem_inv_rows[1]) > lim_rows)
+        return MONC_PROJ_EUNSUPPORTED;
+    const SolveKernels ks = pick_kernels<R>(p);
     const KernelFn fns[] = {ks.fwd_rows, ks.fwd_cols, ks.inv_cols, ks.inv_rows};
-    for (KernelFn f : fns)
-        if (cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax) !=
+    const size_t lims[] = {kSmemMax, lim_cols, lim_cols, lim_rows};
+    for (int i = 0; i < 4; ++i)
+        if (cudaFuncSetAttribute((const void*)fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lims[i]) !=
             cudaSuccess) {
             cudaGetLastError();
             return MONC_PROJ_ECUDA;
@@ -341,6 +382,15 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
 
     const bool fp64 = precision == MONC_PROJ_FP64;
     const size_t csz = fp64 ? 16 : 8;
+    {
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) {
+            cudaGetLastError();
+            nsm = 1;
+        }
+        p->nsm = nsm;
+    }
 
     // ---- host tables
     std::vector<double> cx(nx), sx(nx), cy(ny), sy(ny);
@@ -450,6 +500,11 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     p->ntiles = (p->nxh + tw - 1) / tw;
     p->thr_cols = cty ? threads_for(tw * ny, E) : 256;
     p->smem_cols = (size_t)(cty ? 1 : 2) * tw * p->bs_col * csz;
+    // compile-time lengths run the persistent column kernels: two input
+    // stages of ny x tw values plus the FFT buffer
+    p->persist_cols = cty;
+    if (cty) p->smem_cols = ((size_t)2 * ny * tw + (size_t)tw * p->bs_col) * csz;
+    p->ct_rows = ctx;
     // inverse row tasks: pairs of rows, one complex transform per channel and
     // row pair; index 0 without phi output (3 channels), 1 with (4 channels)
     for (int idx = 0; idx < 2; ++idx) {
@@ -460,6 +515,13 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
         p->rows_inv[idx] = 2 * pairs;
         p->thr_inv_rows[idx] = ctx ? threads_for(np * nx, E) : 256;
         p->smem_inv_rows[idx] = (size_t)(ctx ? 1 : 2) * np * p->bs_row * csz;
+        if (ctx) {
+            // one channel per task: rows_inv rows = rows_inv/2 transforms
+            int npr = std::max(1, std::min({16, 256 * E / nx, (ny + 1) / 2}));
+            p->rows_inv[idx] = 2 * npr;
+            p->thr_inv_rows[idx] = threads_for(npr * nx, E);
+            p->smem_inv_rows[idx] = (size_t)npr * p->bs_row * csz;
+        }
     }
 
     // ---- workspace layout
@@ -471,6 +533,7 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     p->off_Tp = off; off = align256(off + L * csz);
     p->off_Tgy = off; off = align256(off + L * csz);
     p->off_Tgz = off; off = align256(off + L * csz);
+    p->off_Tphi = off; off = align256(off + L * csz);
     p->off_Y = off;                                   // (unused)
     p->off_Gp = off; if (!fp64) off = align256(off + L * 8);   // 1/e of FP64 columns (mixed)
     p->ws_bytes = off;
