@@ -127,6 +127,8 @@ def phase_bytes(g, phase: str, elem: int) -> float:
         "tridiag": 3 * spec,                            # D^ -> p^, gz^
         "inv_cols": 5 * spec,                           # p^, gz^ -> 3 channel spectra
         "inv_rows": 3 * spec + 2 * fields_in,           # 3 spectra + u,v,w -> u,v,w
+        "fwd_fused": fields_in + spec,                  # u,v,w -> D^ (x-spectra stay in L2)
+        "inv_fused": 2 * spec + 2 * fields_in,          # p^, gz^, u,v,w -> u,v,w
     }[phase]
 
 
@@ -357,7 +359,7 @@ def main():
         return
 
     # ---- roofline of the dominant kernel
-    phases = prof["phases"]
+    phases = {k: v for k, v in prof["phases"].items() if v > 0}
     nsolves = prof["solves"]
     dom = max(phases, key=lambda k: phases[k])
     dom_ms = phases[dom] / max(nsolves, 1)

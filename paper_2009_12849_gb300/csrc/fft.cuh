@@ -327,7 +327,9 @@ __device__ __forceinline__ void bfly_map(int t, int nb, int& b, int& q) {
     else { b = t / NQ; q = t - b * NQ; }
 }
 
-template <typename R, int N, int S, bool BFAST, class Load>
+// SYNC_IN: the inputs are read from the same shared buffer the stage writes,
+// so the block synchronises between the reads and the writes.
+template <typename R, int N, int S, bool BFAST, bool SYNC_IN = false, class Load>
 __device__ __forceinline__ void ct_first(cplx<R>* buf, int nb, int bstride, Load&& load) {
     using SI = StageInfo<R, N, 1>;
     constexpr int RAD = SI::RAD, NQ = SI::NQ;
@@ -345,6 +347,7 @@ __device__ __forceinline__ void ct_first(cplx<R>* buf, int nb, int bstride, Load
             for (int r = 0; r < RAD; ++r) x[i][r] = load(b, q + r * NQ);
         }
     }
+    if (SYNC_IN) __syncthreads();
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
         const int t = threadIdx.x + i * blockDim.x;

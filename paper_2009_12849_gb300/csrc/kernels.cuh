@@ -40,6 +40,9 @@ struct ProjParams {
     void* S; void* G; void* T; void* Tp; void* Tgy; void* Tgz; void* Tphi;
     double2* Y; double* Gp;
     int* err;
+    unsigned* sync;             // fused kernels: tickets and per-level counters (zeroed per solve)
+    int ring;                   // levels in the intermediate rings (fused) or nz
+    int lag;                    // fused kernels: levels between producer and consumer tasks
     // task shapes
     int rows_fwd;               // real rows per forward row task (even)
     int nrb_fwd;                // row tasks per level (forward)
@@ -391,6 +394,90 @@ __device__ __forceinline__ void tridiag_column_mixed64(const ProjParams& p, size
     }
 }
 
+// FP32 column without a stored forward sweep: the forward sweep keeps only a
+// checkpoint (y, 1/e) at the start of every kTriSeg levels (thread-local
+// memory); the back substitution recomputes each segment's forward values in
+// registers from its checkpoint, re-reading D'.  D' is read twice, but y and
+// 1/e never travel to DRAM and back.
+constexpr int kTriSeg = 16;
+constexpr int kTriMaxSeg = 64;               // nz <= kTriSeg * kTriMaxSeg
+
+__device__ __forceinline__ void tridiag_column_ckpt32(const ProjParams& p, size_t base, float lam) {
+    using C = float2;
+    const int nz = p.nz;
+    const size_t LS = (size_t)p.ny * p.nxp;
+    C* S = (C*)p.S;
+    C* G = (C*)p.G;
+    const VCoef<float> vc(p);
+    const float scale = (float)p.scale;
+    float ck_g[kTriMaxSeg];
+    C ck_y[kTriMaxSeg];
+    float g = 0.f;
+    C y = make_float2(0.f, 0.f);
+    const int nseg = (nz + kTriSeg - 1) / kTriSeg;
+    // forward sweep, checkpoints at segment starts
+    for (int sg = 0; sg < nseg; ++sg) {
+        ck_g[sg] = g;
+        ck_y[sg] = y;
+        const int k0 = sg * kTriSeg;
+        C d[kTriSeg];
+#pragma unroll
+        for (int i = 0; i < kTriSeg; ++i) d[i] = (k0 + i < nz) ? S[(k0 + i) * LS + base] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < kTriSeg; ++i) {
+            const int k = k0 + i;
+            if (k < nz) {
+                const float ak = vc.a[k];
+                const float m = ak * g;
+                const float e = lam * vc.s[k] - vc.c[k] - ak * m;
+                g = 1.f / e;
+                y = make_float2(d[i].x - m * y.x, d[i].y - m * y.y);
+            }
+        }
+    }
+    // back substitution segment by segment, top to bottom
+    C ph = make_float2(y.x * g, y.y * g);
+    bool top = true;
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+        const int k0 = sg * kTriSeg;
+        C d[kTriSeg], ys[kTriSeg];
+        float gs[kTriSeg];
+#pragma unroll
+        for (int i = 0; i < kTriSeg; ++i) d[i] = (k0 + i < nz) ? S[(k0 + i) * LS + base] : make_float2(0.f, 0.f);
+        float gg = ck_g[sg];
+        C yy = ck_y[sg];
+#pragma unroll
+        for (int i = 0; i < kTriSeg; ++i) {
+            const int k = k0 + i;
+            if (k < nz) {
+                const float ak = vc.a[k];
+                const float m = ak * gg;
+                const float e = lam * vc.s[k] - vc.c[k] - ak * m;
+                gg = 1.f / e;
+                yy = make_float2(d[i].x - m * yy.x, d[i].y - m * yy.y);
+            }
+            ys[i] = yy;
+            gs[i] = gg;
+        }
+#pragma unroll
+        for (int i = kTriSeg - 1; i >= 0; --i) {
+            const int k = k0 + i;
+            if (k >= nz) continue;
+            if (top) {                       // the top level: p = y g
+                top = false;
+                __stcs(&S[k * LS + base], make_float2(ph.x * scale, ph.y * scale));
+                continue;
+            }
+            const float a1 = vc.a[k + 1];
+            const C pn = make_float2((ys[i].x - a1 * ph.x) * gs[i], (ys[i].y - a1 * ph.y) * gs[i]);
+            const float iz = vc.iz[k + 1] * scale;
+            __stcs(&G[(k + 1) * LS + base], make_float2((ph.x - pn.x) * iz, (ph.y - pn.y) * iz));
+            __stcs(&S[k * LS + base], make_float2(pn.x * scale, pn.y * scale));
+            ph = pn;
+        }
+    }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(128) k_tridiag(ProjParams p) {
     const int nxw = (p.nxh + 31) & ~31;
@@ -405,7 +492,9 @@ __global__ void __launch_bounds__(128) k_tridiag(ProjParams p) {
         tridiag_column_inplace<double>(p, base, lam, mean);
     } else {
         const double lam_warp = p.lamx[kx & ~31] + p.lamy[ky];   // smallest |lambda| of the warp
-        if (-lam_warp < p.lam_fp64) tridiag_column_mixed64(p, base, lam, mean);
+        // the warp holding the mean column always runs FP64 (it carries the pin)
+        if (-lam_warp < p.lam_fp64 || (ky == 0 && kx < 32)) tridiag_column_mixed64(p, base, lam, mean);
+        else if (p.nz <= kTriSeg * kTriMaxSeg) tridiag_column_ckpt32(p, base, (float)lam);
         else tridiag_column_inplace<float>(p, base, (float)lam, mean);
     }
 }

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -14,6 +15,7 @@
 
 #include "kernels.cuh"
 #include "persist.cuh"
+#include "fused.cuh"
 
 using namespace mp;
 
@@ -40,6 +42,13 @@ struct monc_proj_plan_s {
     int nsm;                              // SMs of the plan's device (persistent grids)
     bool persist_cols;                    // compile-time lengths: persistent cp.async column kernels
     bool ct_rows;                         // compile-time length along x
+    bool fused;                           // square compile-time grid: fused persistent kernels
+    int ring;                             // levels in the L2 rings of the fused kernels
+    int lag;                              // producer/consumer lag of the fused kernels
+    int grid_fwd_fused, grid_inv_fused;
+    int thr_fwd_fused, thr_inv_fused[2];
+    size_t smem_fwd_fused, smem_inv_fused[2];
+    size_t off_sync, sync_bytes;
     int bs_row, bs_col;
     size_t smem_fwd_rows, smem_cols, smem_inv_rows[2];
     // workspace layout
@@ -49,32 +58,42 @@ struct monc_proj_plan_s {
     bool profiling;
     int nprof;
     std::vector<cudaEvent_t> prof_events;
+    std::vector<unsigned> prof_mask;
 };
 
 namespace {
 
-constexpr int kPhases = 5;
-const char* const kPhaseNames[kPhases] = {"fwd_rows", "fwd_cols", "tridiag", "inv_cols", "inv_rows"};
+constexpr int kPhases = 7;
+const char* const kPhaseNames[kPhases] = {"fwd_rows", "fwd_cols", "tridiag", "inv_cols", "inv_rows",
+                                          "fwd_fused", "inv_fused"};
 
-// Event slot for phase boundary `b` (0..kPhases) of the current solve, or null.
+// Start/end events of every phase of one recorded solve (null when not recording).
 struct PhaseMarks {
-    cudaEvent_t* ev = nullptr;
-    void mark(int b, cudaStream_t st) const { if (ev) cudaEventRecord(ev[b], st); }
+    cudaEvent_t* ev = nullptr;       // [kPhases][2]
+    unsigned* mask = nullptr;        // phases recorded in this solve
+    void start(int ph, cudaStream_t st) const {
+        if (ev) { cudaEventRecord(ev[2 * ph], st); *mask |= 1u << ph; }
+    }
+    void end(int ph, cudaStream_t st) const { if (ev) cudaEventRecord(ev[2 * ph + 1], st); }
 };
 
 PhaseMarks begin_marks(monc_proj_plan_s* p) {
     PhaseMarks m;
     if (!p->profiling || p->nprof >= MONC_PROJ_PROFILE_MAX) return m;
-    const size_t need = (size_t)(p->nprof + 1) * (kPhases + 1);
+    const size_t need = (size_t)(p->nprof + 1) * (2 * kPhases);
     while (p->prof_events.size() < need) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) return m;
         p->prof_events.push_back(e);
     }
-    m.ev = &p->prof_events[(size_t)p->nprof * (kPhases + 1)];
+    if (p->prof_mask.size() < (size_t)p->nprof + 1) p->prof_mask.resize(p->nprof + 1);
+    m.ev = &p->prof_events[(size_t)p->nprof * (2 * kPhases)];
+    m.mask = &p->prof_mask[p->nprof];
+    *m.mask = 0;
     p->nprof++;
     return m;
 }
+
 constexpr size_t kSmemMax = 200 * 1024;
 constexpr size_t kSmemPersist = 220 * 1024;
 // Mixed plans: a3 runs in FP64 for columns with |lambda| < kFp64Fraction * v_max.
@@ -122,6 +141,13 @@ FftFactors factorize(int n, int maxrad) {
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// The fused persistent kernels are opt-in (MONC_PROJ_FUSED=1 in the
+// environment): on GB300 they measured slower than the split kernels.
+bool fused_disabled() {
+    const char* e = std::getenv("MONC_PROJ_FUSED");
+    return !(e && e[0] == '1');
+}
 
 // Block size for a batch of `elems` transform elements at E per thread.
 int threads_for(int elems, int E) {
@@ -192,6 +218,8 @@ void pad_blob(std::vector<unsigned char>& blob) {
     while (blob.size() % 256) blob.push_back(0);
 }
 
+int nz_all_levels(const monc_proj_plan_s* p) { return p->nz; }
+
 ProjParams make_params(const monc_proj_plan_s* p, const void* u, const void* v, const void* w,
                        void* uo, void* vo, void* wo, void* phi, void* ws) {
     ProjParams q{};
@@ -209,6 +237,9 @@ ProjParams make_params(const monc_proj_plan_s* p, const void* u, const void* v, 
     q.S = b + p->off_S; q.G = b + p->off_G; q.T = b + p->off_T;
     q.Tp = b + p->off_Tp; q.Tgy = b + p->off_Tgy; q.Tgz = b + p->off_Tgz; q.Tphi = b + p->off_Tphi;
     q.Y = (double2*)(b + p->off_Y); q.Gp = (double*)(b + p->off_Gp);
+    q.sync = (unsigned*)(b + p->off_sync);
+    q.ring = p->fused ? p->ring : nz_all_levels(p);
+    q.lag = p->lag;
     q.err = p->err;
     q.rows_fwd = p->rows_fwd; q.nrb_fwd = p->nrb_fwd;
     q.tw_cols = p->tw_cols; q.ntiles = p->ntiles;
@@ -299,26 +330,88 @@ template <typename R> SolveKernels pick_kernels(const monc_proj_plan_s* p) {
                         pick_k_inv_rows<R>(nx)};
 }
 
+template <typename R> KernelFn pick_fwd_fused(int n) {
+    if constexpr (sizeof(R) == 8) {
+        switch (n) {
+            case 64: return k_fwd_fused<R, 64>;
+            case 128: return k_fwd_fused<R, 128>;
+            case 256: return k_fwd_fused<R, 256>;
+            case 1024: return k_fwd_fused<R, 1024>;
+            default: return nullptr;
+        }
+    } else {
+        switch (n) {
+            case 64: return k_fwd_fused<R, 64>;
+            case 96: return k_fwd_fused<R, 96>;
+            case 128: return k_fwd_fused<R, 128>;
+            case 192: return k_fwd_fused<R, 192>;
+            case 256: return k_fwd_fused<R, 256>;
+            case 512: return k_fwd_fused<R, 512>;
+            case 1024: return k_fwd_fused<R, 1024>;
+            default: return nullptr;
+        }
+    }
+}
+template <typename R> KernelFn pick_inv_fused(int n) {
+    if constexpr (sizeof(R) == 8) {
+        switch (n) {
+            case 64: return k_inv_fused<R, 64>;
+            case 128: return k_inv_fused<R, 128>;
+            case 256: return k_inv_fused<R, 256>;
+            case 1024: return k_inv_fused<R, 1024>;
+            default: return nullptr;
+        }
+    } else {
+        switch (n) {
+            case 64: return k_inv_fused<R, 64>;
+            case 96: return k_inv_fused<R, 96>;
+            case 128: return k_inv_fused<R, 128>;
+            case 192: return k_inv_fused<R, 192>;
+            case 256: return k_inv_fused<R, 256>;
+            case 512: return k_inv_fused<R, 512>;
+            case 1024: return k_inv_fused<R, 1024>;
+            default: return nullptr;
+        }
+    }
+}
+
 template <typename R>
 int launch_solve(monc_proj_plan_s* p, const ProjParams& q, cudaStream_t st) {
     const int nz = p->nz;
-    const SolveKernels ks = pick_kernels<R>(p);
     const int inv_idx = (q.nch == 4) ? 1 : 0;
-    const int n_fcols = nz * p->ntiles, n_icols = nz * p->ntiles * q.nch;
-    const int n_irows = nz * q.nrb_inv * (p->ct_rows ? q.nch : 1);
     const PhaseMarks pm = begin_marks(p);
-    pm.mark(0, st);
-    ks.fwd_rows<<<nz * p->nrb_fwd, p->thr_fwd_rows, p->smem_fwd_rows, st>>>(q);
-    pm.mark(1, st);
-    ks.fwd_cols<<<p->persist_cols ? std::min(n_fcols, p->nsm) : n_fcols, p->thr_cols, p->smem_cols, st>>>(q);
-    pm.mark(2, st);
     const long long ncol = (long long)p->ny * ((p->nxh + 31) & ~31);
-    k_tridiag<R><<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(q);
-    pm.mark(3, st);
-    ks.inv_cols<<<p->persist_cols ? std::min(n_icols, p->nsm) : n_icols, p->thr_cols, p->smem_cols, st>>>(q);
-    pm.mark(4, st);
-    ks.inv_rows<<<n_irows, p->thr_inv_rows[inv_idx], p->smem_inv_rows[inv_idx], st>>>(q);
-    pm.mark(5, st);
+    if (p->fused) {
+        if (cudaMemsetAsync(q.sync, 0, p->sync_bytes, st) != cudaSuccess) { cudaGetLastError(); return MONC_PROJ_ECUDA; }
+        pm.start(5, st);
+        pick_fwd_fused<R>(p->nx)<<<p->grid_fwd_fused, p->thr_fwd_fused, p->smem_fwd_fused, st>>>(q);
+        pm.end(5, st);
+        pm.start(2, st);
+        k_tridiag<R><<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(q);
+        pm.end(2, st);
+        pm.start(6, st);
+        pick_inv_fused<R>(p->nx)<<<p->grid_inv_fused, p->thr_inv_fused[inv_idx], p->smem_inv_fused[inv_idx], st>>>(q);
+        pm.end(6, st);
+    } else {
+        const SolveKernels ks = pick_kernels<R>(p);
+        const int n_fcols = nz * p->ntiles, n_icols = nz * p->ntiles * q.nch;
+        const int n_irows = nz * q.nrb_inv * (p->ct_rows ? q.nch : 1);
+        pm.start(0, st);
+        ks.fwd_rows<<<nz * p->nrb_fwd, p->thr_fwd_rows, p->smem_fwd_rows, st>>>(q);
+        pm.end(0, st);
+        pm.start(1, st);
+        ks.fwd_cols<<<p->persist_cols ? std::min(n_fcols, p->nsm) : n_fcols, p->thr_cols, p->smem_cols, st>>>(q);
+        pm.end(1, st);
+        pm.start(2, st);
+        k_tridiag<R><<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(q);
+        pm.end(2, st);
+        pm.start(3, st);
+        ks.inv_cols<<<p->persist_cols ? std::min(n_icols, p->nsm) : n_icols, p->thr_cols, p->smem_cols, st>>>(q);
+        pm.end(3, st);
+        pm.start(4, st);
+        ks.inv_rows<<<n_irows, p->thr_inv_rows[inv_idx], p->smem_inv_rows[inv_idx], st>>>(q);
+        pm.end(4, st);
+    }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MONC_PROJ_OK : MONC_PROJ_ECUDA;
 }
@@ -344,8 +437,37 @@ int set_kernel_attrs(const monc_proj_plan_s* p) {
     return MONC_PROJ_OK;
 }
 
-int plan_kernel_attrs(const monc_proj_plan_s* p) {
-    return p->precision == MONC_PROJ_FP64 ? set_kernel_attrs<double>(p) : set_kernel_attrs<float>(p);
+// Fused path: raise the shared-memory limits and size the persistent grids
+// from the occupancy of each kernel.
+template <typename R>
+int setup_fused(monc_proj_plan_s* p) {
+    const KernelFn ff = pick_fwd_fused<R>(p->nx), fi = pick_inv_fused<R>(p->nx);
+    if (!ff || !fi) { p->fused = false; return MONC_PROJ_OK; }
+    const size_t smi = std::max(p->smem_inv_fused[0], p->smem_inv_fused[1]);
+    if (p->smem_fwd_fused > kSmemMax || smi > kSmemMax) { p->fused = false; return MONC_PROJ_OK; }
+    if (cudaFuncSetAttribute((const void*)ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax) != cudaSuccess ||
+        cudaFuncSetAttribute((const void*)fi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax) != cudaSuccess) {
+        cudaGetLastError();
+        return MONC_PROJ_ECUDA;
+    }
+    int bf = 0, bi = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, (const void*)ff, p->thr_fwd_fused, p->smem_fwd_fused) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bi, (const void*)fi, std::max(p->thr_inv_fused[0], p->thr_inv_fused[1]),
+                                                      smi) != cudaSuccess) {
+        cudaGetLastError();
+        return MONC_PROJ_ECUDA;
+    }
+    if (bf < 1 || bi < 1) { p->fused = false; return MONC_PROJ_OK; }
+    p->grid_fwd_fused = bf * p->nsm;
+    p->grid_inv_fused = bi * p->nsm;
+    return MONC_PROJ_OK;
+}
+
+int plan_kernel_attrs(monc_proj_plan_s* p) {
+    const int r = p->precision == MONC_PROJ_FP64 ? set_kernel_attrs<double>(p) : set_kernel_attrs<float>(p);
+    if (r != MONC_PROJ_OK || !p->fused) return r;
+    return p->precision == MONC_PROJ_FP64 ? setup_fused<double>(p) : setup_fused<float>(p);
 }
 
 // Argument checks shared by every entry point that takes grid arguments.
@@ -524,6 +646,22 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
         }
     }
 
+    // fused persistent kernels for square compile-time grids: one block size
+    // and shared-memory size for both task kinds of each kernel
+    p->fused = ctx && cty && nx == ny && !fused_disabled();
+    p->ring = std::min(nz, fp64 ? 4 : 8);
+    p->thr_fwd_fused = std::max(p->thr_fwd_rows, p->thr_cols);
+    p->smem_fwd_fused = std::max((size_t)npair * p->bs_row * csz, (size_t)tw * p->bs_col * csz);
+    for (int idx = 0; idx < 2; ++idx) {
+        p->thr_inv_fused[idx] = std::max(p->thr_inv_rows[idx], p->thr_cols);
+        p->smem_inv_fused[idx] = std::max({p->smem_inv_rows[idx], (size_t)tw * p->bs_col * csz,
+                                           (size_t)ny * tw * csz});
+    }
+    // consumers trail producers by `lag` levels; a ring of lag + 3 levels
+    // lets producers run ahead without waiting for slots
+    p->lag = std::min(nz, 3);
+    if (p->fused) p->ring = std::min(nz, p->lag + 3);
+
     // ---- workspace layout
     const size_t L = (size_t)nz * ny * p->nxp;
     size_t off = 0;
@@ -536,6 +674,9 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     p->off_Tphi = off; off = align256(off + L * csz);
     p->off_Y = off;                                   // (unused)
     p->off_Gp = off; if (!fp64) off = align256(off + L * 8);   // 1/e of FP64 columns (mixed)
+    p->off_sync = off;                                // tickets and per-level counters of the fused kernels
+    p->sync_bytes = (size_t)(2 + 10 * nz) * sizeof(unsigned);
+    off = align256(off + p->sync_bytes);
     p->ws_bytes = off;
 }
 
@@ -677,13 +818,13 @@ int monc_proj_profile_read(monc_proj_plan_t plan, int max_phases, double* total_
     if (nphases) *nphases = kPhases;
     if (nsolves) *nsolves = plan->nprof;
     if (plan->nprof == 0) return MONC_PROJ_OK;
-    const cudaEvent_t last = plan->prof_events[(size_t)plan->nprof * (kPhases + 1) - 1];
-    if (cudaEventSynchronize(last) != cudaSuccess) return MONC_PROJ_ECUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return MONC_PROJ_ECUDA;
     for (int s = 0; s < plan->nprof; ++s) {
-        const cudaEvent_t* ev = &plan->prof_events[(size_t)s * (kPhases + 1)];
+        const cudaEvent_t* ev = &plan->prof_events[(size_t)s * (2 * kPhases)];
         for (int ph = 0; ph < kPhases && ph < max_phases; ++ph) {
+            if (!(plan->prof_mask[s] & (1u << ph))) continue;
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, ev[ph], ev[ph + 1]) != cudaSuccess) return MONC_PROJ_ECUDA;
+            if (cudaEventElapsedTime(&ms, ev[2 * ph], ev[2 * ph + 1]) != cudaSuccess) return MONC_PROJ_ECUDA;
             total_ms[ph] += ms;
         }
     }
