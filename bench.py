@@ -46,6 +46,9 @@ def parse_args():
     ap.add_argument("--no-check", action="store_true", help="skip the accuracy check")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batch measurement")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the serving measurement (0 skips it; the full recipe is 10000)")
     return ap.parse_args()
 
 
@@ -348,6 +351,22 @@ def main():
         P64.close()
         del u64, v64, w64, o64
 
+    # ---- uneven batch of 64 projections (one batched call, and its CUDA-graph replay)
+    batch = None
+    if not args.no_batch and rank == 0:
+        batch = measure_batch(dev, stream)
+
+    # ---- serving: Poisson arrivals, continuous batching, HBM admission
+    serving = None
+    if args.serve_requests > 0 and rank == 0:
+        from paper_2009_12849_gb300 import serve as S
+        srv = S.ProjectionServer(dev, hbm_budget=40e9, slots=32)
+        reqs = S.requests_from_recipe(args.serve_requests, 2000.0, 4)
+        serving = srv.run(reqs)
+        serving.update({"rate_per_s": 2000.0, "recipe": "sizes 128-512 log-uniform (nearest 2^a3^b5^c) "
+                                                       "x nz 64-192, seed 4, mixed precision"})
+        srv.close()
+
     # ---- accuracy of the timed result against the oracle (sampled modes + divergence)
     check = None
     if not args.no_check and rank == 0:
@@ -399,12 +418,57 @@ def main():
         "clocks": clk,
         "gpu_launches": nsolves * len(phases),
         "fp64_path": fp64,
+        "batch": batch,
+        "serving": serving,
         "accuracy": check,
         "device_status": status,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def measure_batch(dev, stream, count=64, reps=5):
+    """64 uneven projections (n from {64,96,128,192,256}, nz from
+    {64,96,128,160}, mixed precision, seed 3): time of one batched call and of
+    a CUDA-graph replay of it."""
+    import torch
+    from paper_2009_12849_gb300 import monc_proj as MP
+    from paper_2009_12849_gb300 import workloads as W
+    inst = W.batch_instances(count, 3)
+    grids = [g for g, _ in inst]
+    B = MP.BatchProjector(grids, "mixed", dev)
+    args = []
+    for g, sd in inst:
+        u, v, w = (torch.from_numpy(a).to(dev) for a in W.random_fields_f32(g, sd, False))
+        args.append((u, v, w, torch.empty_like(u), torch.empty_like(v), torch.empty_like(w)))
+    pts = sum(g.npoints for g in grids)
+    for _ in range(2):
+        B.solve(args, stream=stream)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        B.solve(args, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    side = torch.cuda.Stream(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            B.solve(args, stream=side)
+    graph.replay()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(reps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_graph = e0.elapsed_time(e1) / reps
+    B.close()
+    return {"instances": count, "points": pts, "ms_per_batch": ms, "mpts_per_s": pts / (ms * 1e-3) / 1e6,
+            "graph_ms_per_batch": ms_graph, "graph_mpts_per_s": pts / (ms_graph * 1e-3) / 1e6}
 
 
 def accuracy_check(g, u_h, v_h, w_h, outs):

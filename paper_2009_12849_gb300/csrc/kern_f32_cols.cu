@@ -1,0 +1,11 @@
+// FP32 column-transform kernels and the vertical solve.
+#include "persist.cuh"
+#include "pickers.h"
+
+namespace mp {
+template <> KernelFn pick_k_fwd_cols<float>(int n) { MP_PICK_F32(k_fwd_cols, (k_fwd_cols<float, 0>)) }
+template <> KernelFn pick_k_inv_cols<float>(int n) { MP_PICK_F32(k_inv_cols, (k_inv_cols<float, 0>)) }
+template <> KernelFn pick_fwd_cols_persist<float>(int n) { MP_PICK_F32(k_cols_persist, nullptr, , false) }
+template <> KernelFn pick_inv_cols_persist<float>(int n) { MP_PICK_F32(k_cols_persist, nullptr, , true) }
+template <> KernelFn pick_tridiag<float>() { return k_tridiag<float>; }
+}  // namespace mp

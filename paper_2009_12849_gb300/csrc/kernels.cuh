@@ -104,7 +104,62 @@ __global__ void __launch_bounds__(512) k_fwd_rows(ProjParams p) {
     const R idx = (R)p.idx, idy = (R)p.idy;
 
     const C* res;
-    {
+    if constexpr (NX > 0 && sizeof(R) == 4) {
+        // FP32, compile-time length: every thread takes groups of 4 adjacent
+        // cells of a row and loads them as float4 (u, v, v of the row below,
+        // w below and above), 4 groups in flight per thread.
+        constexpr int G = 4, NG = NX / 4;
+        const int tot = p.rows_fwd * NG;
+        const int step = G * blockDim.x;
+        for (int base = threadIdx.x; base < tot; base += step) {
+            float4 u4[G], v4[G], vm4[G], wl4[G], wh4[G];
+            float um1[G];
+#pragma unroll
+            for (int c = 0; c < G; ++c) {
+                const int t = base + c * blockDim.x;
+                const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                u4[c] = v4[c] = vm4[c] = wl4[c] = wh4[c] = z;
+                um1[c] = 0.f;
+                if (t < tot) {
+                    const int r = t / NG;
+                    const int i0 = 4 * (t - r * NG);
+                    const int j = j0 + r;
+                    if (j < ny) {
+                        const size_t row = (size_t)k * plane + (size_t)j * NX;
+                        const size_t rowm = (size_t)k * plane + (size_t)(j == 0 ? ny - 1 : j - 1) * NX;
+                        u4[c] = *(const float4*)&u[row + i0];
+                        um1[c] = u[row + (i0 == 0 ? NX - 1 : i0 - 1)];
+                        v4[c] = *(const float4*)&v[row + i0];
+                        vm4[c] = *(const float4*)&v[rowm + i0];
+                        if (k > 0) wl4[c] = *(const float4*)&w[row + i0];
+                        if (k < nz - 1) wh4[c] = *(const float4*)&w[row + plane + i0];
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < G; ++c) {
+                const int t = base + c * blockDim.x;
+                if (t < tot) {
+                    const int r = t / NG;
+                    const int i0 = 4 * (t - r * NG);
+                    const float uu[5] = {um1[c], u4[c].x, u4[c].y, u4[c].z, u4[c].w};
+                    const float vv[4] = {v4[c].x, v4[c].y, v4[c].z, v4[c].w};
+                    const float vm[4] = {vm4[c].x, vm4[c].y, vm4[c].z, vm4[c].w};
+                    const float wl[4] = {wl4[c].x, wl4[c].y, wl4[c].z, wl4[c].w};
+                    const float wh[4] = {wh4[c].x, wh4[c].y, wh4[c].z, wh4[c].w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float hdiv = (uu[e + 1] - uu[e]) * (float)idx + (vv[e] - vm[e]) * (float)idy;
+                        const float d = (float)sv * hdiv + ((float)rhi * wh[e] - (float)rlo * wl[e]);
+                        float* slot = (float*)&bufA[(r >> 1) * bs + spad(i0 + e)];
+                        slot[r & 1] = d;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        res = run_fft<R, NX, -1>(bufA, npair, bs, p.fx, ctab<R>(p.twx));
+    } else {
         // Loads are batched (kLoadBatch elements per thread issued before any is
         // used) so that enough bytes are in flight to cover DRAM latency.
         const int tot = p.rows_fwd * nx;

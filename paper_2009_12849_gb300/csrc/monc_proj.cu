@@ -13,9 +13,7 @@
 #include <new>
 #include <vector>
 
-#include "kernels.cuh"
-#include "persist.cuh"
-#include "fused.cuh"
+#include "pickers.h"
 
 using namespace mp;
 
@@ -50,7 +48,7 @@ struct monc_proj_plan_s {
     size_t smem_fwd_fused, smem_inv_fused[2];
     size_t off_sync, sync_bytes;
     int bs_row, bs_col;
-    size_t smem_fwd_rows, smem_cols, smem_inv_rows[2];
+    size_t smem_fwd_rows, smem_cols, smem_fcols, smem_inv_rows[2];
     // workspace layout
     size_t ws_bytes;
     size_t off_S, off_G, off_T, off_Tp, off_Tgy, off_Tgz, off_Tphi, off_Y, off_Gp;
@@ -254,69 +252,11 @@ ProjParams make_params(const monc_proj_plan_s* p, const void* u, const void* v, 
 // Kernel selection: lengths with a compile-time FFT plan get their own
 // instantiation; every other 2^a 3^b 5^c length runs the run-time plan.
 // ---------------------------------------------------------------------------
-using KernelFn = void (*)(ProjParams);
-
 bool ct_length(int n, bool fp64) {
     if (fp64) return n == 64 || n == 128 || n == 256 || n == 1024;
     return n == 64 || n == 96 || n == 128 || n == 192 || n == 256 || n == 512 || n == 1024;
 }
 
-
-#define MP_KERNEL_PICKER(NAME)                                                              \
-    template <typename R> KernelFn pick_##NAME(int n) {                                     \
-        if constexpr (sizeof(R) == 8) {                                                     \
-            switch (n) {                                                                    \
-                case 64: return NAME<R, 64>;                                                \
-                case 128: return NAME<R, 128>;                                              \
-                case 256: return NAME<R, 256>;                                              \
-                case 1024: return NAME<R, 1024>;                                            \
-                default: return NAME<R, 0>;                                                 \
-            }                                                                               \
-        } else {                                                                            \
-            switch (n) {                                                                    \
-                case 64: return NAME<R, 64>;                                                \
-                case 96: return NAME<R, 96>;                                                \
-                case 128: return NAME<R, 128>;                                              \
-                case 192: return NAME<R, 192>;                                              \
-                case 256: return NAME<R, 256>;                                              \
-                case 512: return NAME<R, 512>;                                              \
-                case 1024: return NAME<R, 1024>;                                            \
-                default: return NAME<R, 0>;                                                 \
-            }                                                                               \
-        }                                                                                   \
-    }
-MP_KERNEL_PICKER(k_fwd_rows)
-MP_KERNEL_PICKER(k_fwd_cols)
-MP_KERNEL_PICKER(k_inv_cols)
-MP_KERNEL_PICKER(k_inv_rows)
-#undef MP_KERNEL_PICKER
-
-#define MP_PERSIST_PICKER(NAME, KERNEL, ...)                                                \
-    template <typename R> KernelFn NAME(int n) {                                            \
-        if constexpr (sizeof(R) == 8) {                                                     \
-            switch (n) {                                                                    \
-                case 64: return KERNEL<R, 64 __VA_ARGS__>;                                  \
-                case 128: return KERNEL<R, 128 __VA_ARGS__>;                                \
-                case 256: return KERNEL<R, 256 __VA_ARGS__>;                                \
-                case 1024: return KERNEL<R, 1024 __VA_ARGS__>;                              \
-                default: return nullptr;                                                    \
-            }                                                                               \
-        } else {                                                                            \
-            switch (n) {                                                                    \
-                case 64: return KERNEL<R, 64 __VA_ARGS__>;                                  \
-                case 96: return KERNEL<R, 96 __VA_ARGS__>;                                  \
-                case 128: return KERNEL<R, 128 __VA_ARGS__>;                                \
-                case 192: return KERNEL<R, 192 __VA_ARGS__>;                                \
-                case 256: return KERNEL<R, 256 __VA_ARGS__>;                                \
-                case 512: return KERNEL<R, 512 __VA_ARGS__>;                                \
-                case 1024: return KERNEL<R, 1024 __VA_ARGS__>;                              \
-                default: return nullptr;                                                    \
-            }                                                                               \
-        }                                                                                   \
-    }
-MP_PERSIST_PICKER(pick_fwd_cols_persist, k_cols_persist, , false)
-MP_PERSIST_PICKER(pick_inv_cols_persist, k_cols_persist, , true)
-#undef MP_PERSIST_PICKER
 
 struct SolveKernels {
     KernelFn fwd_rows, fwd_cols, inv_cols, inv_rows;
@@ -325,54 +265,9 @@ struct SolveKernels {
 template <typename R> SolveKernels pick_kernels(const monc_proj_plan_s* p) {
     const int nx = p->nx, ny = p->ny;
     return SolveKernels{pick_k_fwd_rows<R>(nx),
-                        p->persist_cols ? pick_fwd_cols_persist<R>(ny) : pick_k_fwd_cols<R>(ny),
+                        pick_k_fwd_cols<R>(ny),
                         p->persist_cols ? pick_inv_cols_persist<R>(ny) : pick_k_inv_cols<R>(ny),
                         pick_k_inv_rows<R>(nx)};
-}
-
-template <typename R> KernelFn pick_fwd_fused(int n) {
-    if constexpr (sizeof(R) == 8) {
-        switch (n) {
-            case 64: return k_fwd_fused<R, 64>;
-            case 128: return k_fwd_fused<R, 128>;
-            case 256: return k_fwd_fused<R, 256>;
-            case 1024: return k_fwd_fused<R, 1024>;
-            default: return nullptr;
-        }
-    } else {
-        switch (n) {
-            case 64: return k_fwd_fused<R, 64>;
-            case 96: return k_fwd_fused<R, 96>;
-            case 128: return k_fwd_fused<R, 128>;
-            case 192: return k_fwd_fused<R, 192>;
-            case 256: return k_fwd_fused<R, 256>;
-            case 512: return k_fwd_fused<R, 512>;
-            case 1024: return k_fwd_fused<R, 1024>;
-            default: return nullptr;
-        }
-    }
-}
-template <typename R> KernelFn pick_inv_fused(int n) {
-    if constexpr (sizeof(R) == 8) {
-        switch (n) {
-            case 64: return k_inv_fused<R, 64>;
-            case 128: return k_inv_fused<R, 128>;
-            case 256: return k_inv_fused<R, 256>;
-            case 1024: return k_inv_fused<R, 1024>;
-            default: return nullptr;
-        }
-    } else {
-        switch (n) {
-            case 64: return k_inv_fused<R, 64>;
-            case 96: return k_inv_fused<R, 96>;
-            case 128: return k_inv_fused<R, 128>;
-            case 192: return k_inv_fused<R, 192>;
-            case 256: return k_inv_fused<R, 256>;
-            case 512: return k_inv_fused<R, 512>;
-            case 1024: return k_inv_fused<R, 1024>;
-            default: return nullptr;
-        }
-    }
 }
 
 template <typename R>
@@ -387,25 +282,30 @@ int launch_solve(monc_proj_plan_s* p, const ProjParams& q, cudaStream_t st) {
         pick_fwd_fused<R>(p->nx)<<<p->grid_fwd_fused, p->thr_fwd_fused, p->smem_fwd_fused, st>>>(q);
         pm.end(5, st);
         pm.start(2, st);
-        k_tridiag<R><<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(q);
+        pick_tridiag<R>()<<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(q);
         pm.end(2, st);
         pm.start(6, st);
         pick_inv_fused<R>(p->nx)<<<p->grid_inv_fused, p->thr_inv_fused[inv_idx], p->smem_inv_fused[inv_idx], st>>>(q);
         pm.end(6, st);
     } else {
         const SolveKernels ks = pick_kernels<R>(p);
-        const int n_fcols = nz * p->ntiles, n_icols = nz * p->ntiles * q.nch;
+        const int n_fcols = nz * p->ntiles;
+    const int n_icols = nz * p->ntiles * (p->persist_cols ? 2 : q.nch);
         const int n_irows = nz * q.nrb_inv * (p->ct_rows ? q.nch : 1);
         pm.start(0, st);
         ks.fwd_rows<<<nz * p->nrb_fwd, p->thr_fwd_rows, p->smem_fwd_rows, st>>>(q);
         pm.end(0, st);
         pm.start(1, st);
-        ks.fwd_cols<<<p->persist_cols ? std::min(n_fcols, p->nsm) : n_fcols, p->thr_cols, p->smem_cols, st>>>(q);
+        ks.fwd_cols<<<n_fcols, p->thr_cols, p->smem_fcols, st>>>(q);
         pm.end(1, st);
         pm.start(2, st);
-        k_tridiag<R><<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(q);
+        pick_tridiag<R>()<<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(q);
         pm.end(2, st);
         pm.start(3, st);
+        if (p->persist_cols && cudaMemsetAsync(q.sync, 0, sizeof(unsigned), st) != cudaSuccess) {
+            cudaGetLastError();
+            return MONC_PROJ_ECUDA;
+        }
         ks.inv_cols<<<p->persist_cols ? std::min(n_icols, p->nsm) : n_icols, p->thr_cols, p->smem_cols, st>>>(q);
         pm.end(3, st);
         pm.start(4, st);
@@ -422,12 +322,12 @@ template <typename R>
 int set_kernel_attrs(const monc_proj_plan_s* p) {
     const size_t lim_cols = p->persist_cols ? kSmemPersist : kSmemMax;
     const size_t lim_rows = kSmemMax;
-    if (p->smem_fwd_rows > kSmemMax || p->smem_cols > lim_cols ||
+    if (p->smem_fwd_rows > kSmemMax || p->smem_cols > lim_cols || p->smem_fcols > kSmemMax ||
         std::max(p->smem_inv_rows[0], p->smem_inv_rows[1]) > lim_rows)
         return MONC_PROJ_EUNSUPPORTED;
     const SolveKernels ks = pick_kernels<R>(p);
     const KernelFn fns[] = {ks.fwd_rows, ks.fwd_cols, ks.inv_cols, ks.inv_rows};
-    const size_t lims[] = {kSmemMax, lim_cols, lim_cols, lim_rows};
+    const size_t lims[] = {kSmemMax, kSmemMax, lim_cols, lim_rows};
     for (int i = 0; i < 4; ++i)
         if (cudaFuncSetAttribute((const void*)fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lims[i]) !=
             cudaSuccess) {
@@ -622,8 +522,9 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     p->ntiles = (p->nxh + tw - 1) / tw;
     p->thr_cols = cty ? threads_for(tw * ny, E) : 256;
     p->smem_cols = (size_t)(cty ? 1 : 2) * tw * p->bs_col * csz;
-    // compile-time lengths run the persistent column kernels: two input
-    // stages of ny x tw values plus the FFT buffer
+    p->smem_fcols = p->smem_cols;
+    // compile-time lengths run the persistent inverse column kernel: two
+    // input stages of ny x tw values plus the FFT buffer
     p->persist_cols = cty;
     if (cty) p->smem_cols = ((size_t)2 * ny * tw + (size_t)tw * p->bs_col) * csz;
     p->ct_rows = ctx;
@@ -691,6 +592,38 @@ void plan_bind(monc_proj_plan_s* p, unsigned char* db, const TableOffsets& to) {
     p->csum32 = (const float*)(db + to.cs32); p->idzn32 = (const float*)(db + to.iz32);
     p->lamy = (const double*)(db + to.ly); p->ex = db + to.ex; p->ey = db + to.ey;
     p->err = (int*)(db + to.err);
+}
+
+// Streams on which a batch's instances run concurrently (per device), with
+// the fork/join events that order them after and before the caller's stream.
+constexpr int kBatchStreams = 16;
+struct StreamPool {
+    std::mutex mu;
+    bool ready = false;
+    cudaStream_t s[kBatchStreams];
+    cudaEvent_t fork;
+    cudaEvent_t join[kBatchStreams];
+};
+constexpr int kPoolMaxDevices = 64;
+std::mutex g_pool_mu;
+StreamPool g_pools[kPoolMaxDevices];
+
+int stream_pool(StreamPool** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return MONC_PROJ_ECUDA; }
+    if (dev < 0 || dev >= kPoolMaxDevices) return MONC_PROJ_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    StreamPool& p = g_pools[dev];
+    if (!p.ready) {
+        bool ok = cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int j = 0; ok && j < kBatchStreams; ++j)
+            ok = cudaStreamCreateWithFlags(&p.s[j], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&p.join[j], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) { cudaGetLastError(); return MONC_PROJ_ECUDA; }
+        p.ready = true;
+    }
+    *out = &p;
+    return MONC_PROJ_OK;
 }
 
 }  // namespace
@@ -779,14 +712,53 @@ int monc_proj_solve_batch(const monc_proj_plan_t* plans, const monc_proj_fields*
     int rc = monc_proj_batch_workspace_size(plans, count, &need);
     if (rc) return rc;
     if (workspace_bytes < need) return MONC_PROJ_EINVAL;
-    unsigned char* ws = (unsigned char*)workspace;
+    if (count == 0) return MONC_PROJ_OK;
     for (int i = 0; i < count; ++i) {
         const monc_proj_fields& f = fields[i];
-        rc = monc_proj_solve(plans[i], f.u, f.v, f.w, f.u_out, f.v_out, f.w_out, f.phi_out, ws, stream);
-        if (rc) return rc;
-        ws += align256(plans[i]->ws_bytes);
+        if (!f.u || !f.v || !f.w || !f.u_out || !f.v_out || !f.w_out) return MONC_PROJ_EINVAL;
     }
-    return MONC_PROJ_OK;
+    StreamPool* pool = nullptr;
+    rc = stream_pool(&pool);
+    if (rc) return rc;
+    // workspace offsets in argument order; launch order largest first so the
+    // round-robin over the pool's streams balances the work
+    std::vector<size_t> off(count);
+    std::vector<int> order(count);
+    size_t o = 0;
+    for (int i = 0; i < count; ++i) {
+        off[i] = o;
+        o += align256(plans[i]->ws_bytes);
+        order[i] = i;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const double na = (double)plans[a]->nx * plans[a]->ny * plans[a]->nz;
+        const double nb = (double)plans[b]->nx * plans[b]->ny * plans[b]->nz;
+        return na > nb;
+    });
+    std::lock_guard<std::mutex> lock(pool->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nstreams = std::min(count, kBatchStreams);
+    if (cudaEventRecord(pool->fork, st) != cudaSuccess) { cudaGetLastError(); return MONC_PROJ_ECUDA; }
+    for (int j = 0; j < nstreams; ++j)
+        if (cudaStreamWaitEvent(pool->s[j], pool->fork, 0) != cudaSuccess) { cudaGetLastError(); return MONC_PROJ_ECUDA; }
+    unsigned char* ws = (unsigned char*)workspace;
+    int first_error = MONC_PROJ_OK;
+    for (int n = 0; n < count; ++n) {
+        const int i = order[n];
+        const monc_proj_fields& f = fields[i];
+        const int r = monc_proj_solve(plans[i], f.u, f.v, f.w, f.u_out, f.v_out, f.w_out, f.phi_out, ws + off[i],
+                                      pool->s[n % nstreams]);
+        if (r && !first_error) first_error = r;
+    }
+    // join: the caller's stream waits for every pool stream used
+    for (int j = 0; j < nstreams; ++j) {
+        if (cudaEventRecord(pool->join[j], pool->s[j]) != cudaSuccess ||
+            cudaStreamWaitEvent(st, pool->join[j], 0) != cudaSuccess) {
+            cudaGetLastError();
+            return MONC_PROJ_ECUDA;
+        }
+    }
+    return first_error;
 }
 
 int monc_proj_sync_status(monc_proj_plan_t plan, void* stream) {

@@ -35,28 +35,30 @@ __global__ void __launch_bounds__(256, 1) k_cols_persist(ProjParams p) {
     constexpr int CPC = 16 / (int)sizeof(C);     // complex values per 16-byte chunk
     const int tw = p.tw_cols, nz = p.nz, ny = p.ny, nxh = p.nxh, nxp = p.nxp;
     const int ntiles = p.ntiles;
-    const int nf = INV ? p.nch : 1;
-    const int ntask = nz * ntiles * nf;
+    // inverse: task kind 0 transforms the staged S tile into every field that
+    // derives from p^ (Tp with ex, Tgy, and Tphi if requested); kind 1 the G tile
+    const int nkind = INV ? 2 : 1;
+    const int ntask = nz * ntiles * nkind;
     C* stage[2] = {(C*)smem_raw, (C*)smem_raw + (size_t)NY * tw};
     C* fbuf = (C*)smem_raw + (size_t)2 * NY * tw;
     const int cpr = tw / CPC;                    // chunks per tile row
 
-    auto decode = [&](int task, int& k, int& kx0, int& f) {
-        f = task % nf;
-        const int t2 = task / nf;
+    auto decode = [&](int task, int& k, int& kx0, int& kind) {
+        kind = task % nkind;
+        const int t2 = task / nkind;
         k = t2 / ntiles;
         kx0 = (t2 - k * ntiles) * tw;
     };
-    auto source = [&](int f) -> const C* {
+    auto source = [&](int kind) -> const C* {
         if (!INV) return (const C*)p.T;
-        return (f == 2) ? (const C*)p.G : (const C*)p.S;
+        return (kind == 1) ? (const C*)p.G : (const C*)p.S;
     };
     const C* ex = ctab<R>(p.ex);
     auto issue = [&](int task, C* st) {
-        int k, kx0, f;
-        decode(task, k, kx0, f);
-        if (INV && f == 2 && k == 0) return;
-        const C* src = source(f);
+        int k, kx0, kind;
+        decode(task, k, kx0, kind);
+        if (INV && kind == 1 && k == 0) return;
+        const C* src = source(kind);
         const int nchunk = NY * cpr;
         for (int c = threadIdx.x; c < nchunk; c += blockDim.x) {
             const int j = c / cpr;
@@ -71,43 +73,66 @@ __global__ void __launch_bounds__(256, 1) k_cols_persist(ProjParams p) {
             }
         }
     };
+    // one transform of the staged tile into dst (f: 0 x-gradient, 1 y-gradient, else plain)
+    auto transform = [&](const C* st, int k, int kx0, int f, C* dst) {
+        const C* ey = (INV && f == 1) ? ctab<R>(p.ey) : nullptr;
+        auto load = [&](int c, int j) -> C {
+            const C v = st[j * tw + c];
+            return ey ? cmul(v, ey[j]) : v;
+        };
+        ct_first<R, NY, S, true>(fbuf, tw, p.bs_col, load);
+        CtMid<R, NY, StageInfo<R, NY, 1>::NEXT, S>::run(fbuf, tw, p.bs_col, ctab<R>(p.twy));
+        const bool mul_ex = INV && f == 0;
+        auto store = [&](int c, int q, const C* x, int ns) {
+            const int kx = kx0 + c;
+            if (kx >= nxh) return;
+            constexpr int RAD = StageInfo<R, NY, LastNs<R, NY>::value>::RAD;
+            const C e = mul_ex ? ex[kx] : cmk<R>((R)1, (R)0);
+#pragma unroll
+            for (int r = 0; r < RAD; ++r)
+                dst[((size_t)k * ny + q + r * ns) * nxp + kx] = mul_ex ? cmul(x[r], e) : x[r];
+        };
+        ct_last<R, NY, S, true>(fbuf, tw, p.bs_col, ctab<R>(p.twy), store);
+        __syncthreads();
+    };
 
-    int task = blockIdx.x;
+    // tasks are handed out by a ticket counter (zeroed before the launch);
+    // a block takes its next ticket before transforming the current task so
+    // that the next tile's copies are in flight meanwhile
+    __shared__ int s_next;
+    unsigned* ticket = p.sync;
+    auto take = [&]() {
+        if (threadIdx.x == 0) s_next = (int)atomicAdd(ticket, 1u);
+        __syncthreads();
+        const int t = s_next;
+        __syncthreads();
+        return t;
+    };
+    int task = take();
     int s = 0;
     if (task < ntask) issue(task, stage[0]);
     cp_async_commit();
-    for (; task < ntask; task += gridDim.x) {
-        const int next = task + gridDim.x;
+    while (task < ntask) {
+        const int next = take();
         if (next < ntask) issue(next, stage[s ^ 1]);
         cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();
-        int k, kx0, f;
-        decode(task, k, kx0, f);
-        if (!(INV && f == 2 && k == 0)) {
-            const C* st = stage[s];
-            const C* ey = (INV && f == 1) ? ctab<R>(p.ey) : nullptr;
-            auto load = [&](int c, int j) -> C {
-                const C v = st[j * tw + c];
-                return ey ? cmul(v, ey[j]) : v;
-            };
-            ct_first<R, NY, S, true>(fbuf, tw, p.bs_col, load);
-            CtMid<R, NY, StageInfo<R, NY, 1>::NEXT, S>::run(fbuf, tw, p.bs_col, ctab<R>(p.twy));
-            C* dst = (C*)p.S;
-            if (INV) dst = (f == 0) ? (C*)p.Tp : (f == 1) ? (C*)p.Tgy : (f == 2) ? (C*)p.Tgz : (C*)p.Tphi;
-            auto store = [&](int c, int q, const C* x, int ns) {
-                const int kx = kx0 + c;
-                if (kx >= nxh) return;
-                constexpr int RAD = StageInfo<R, NY, LastNs<R, NY>::value>::RAD;
-                const C scale = (INV && f == 0) ? ex[kx] : cmk<R>((R)1, (R)0);
-#pragma unroll
-                for (int r = 0; r < RAD; ++r)
-                    dst[((size_t)k * ny + q + r * ns) * nxp + kx] = (INV && f == 0) ? cmul(x[r], scale) : x[r];
-            };
-            ct_last<R, NY, S, true>(fbuf, tw, p.bs_col, ctab<R>(p.twy), store);
+        int k, kx0, kind;
+        decode(task, k, kx0, kind);
+        const C* st = stage[s];
+        if (!INV) {
+            transform(st, k, kx0, -1, (C*)p.S);
+        } else if (kind == 0) {
+            transform(st, k, kx0, 0, (C*)p.Tp);
+            transform(st, k, kx0, 1, (C*)p.Tgy);
+            if (p.nch == 4) transform(st, k, kx0, 3, (C*)p.Tphi);
+        } else if (k > 0) {
+            transform(st, k, kx0, 2, (C*)p.Tgz);
         }
         __syncthreads();
         s ^= 1;
+        task = next;
     }
     cp_async_wait<0>();
 }

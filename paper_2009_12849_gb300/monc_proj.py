@@ -277,3 +277,51 @@ class Projector:
             self.close()
         except Exception:
             pass
+
+
+class Plan:
+    """A plan handle without a workspace (for batched and served solves)."""
+
+    def __init__(self, grid, precision="mixed", device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        with torch.cuda.device(self.device):
+            self.handle = monc_proj_plan(grid.nx, grid.ny, grid.nz, grid.dx, grid.dy, grid.dz, grid.rho_c,
+                                         grid.rho_f, precision)
+        self.grid = grid
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.dtype = DTYPES[self.precision]
+        self.workspace_bytes = monc_proj_workspace_size(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            monc_proj_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchProjector:
+    """Uneven batch of independent projections, solved together by
+    monc_proj_solve_batch (the instances run concurrently on the device)."""
+
+    def __init__(self, grids, precision="mixed", device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        with torch.cuda.device(self.device):
+            self.plans = [Plan(g, precision, self.device) for g in grids]
+            self.workspace_bytes = monc_proj_batch_workspace_size([p.handle for p in self.plans])
+            self.workspace = torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8, device=self.device)
+
+    def solve(self, fields, stream=None):
+        """fields: list of (u, v, w, u_out, v_out, w_out) or (..., phi_out) tensors."""
+        if len(fields) != len(self.plans):
+            raise ProjError(MONC_PROJ_EINVAL, "BatchProjector.solve")
+        full = [tuple(f) + (None,) * (7 - len(f)) for f in fields]
+        monc_proj_solve_batch([p.handle for p in self.plans], full, self.workspace, stream)
+
+    def close(self):
+        for p in self.plans:
+            p.close()

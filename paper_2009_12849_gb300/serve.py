@@ -1,0 +1,249 @@
+"""Continuous-batching server for projection requests of different grid sizes.
+
+Requests arrive over time (each with an arrival time, a square horizontal
+size n, a level count nz and a seed for its synthetic fields).  The loop
+
+* moves arrived requests into a FIFO queue,
+* admits queued requests while the HBM budget (fields + workspace of every
+  request on the device) and the stream slots allow, even while earlier
+  requests are still running: each admitted request runs on its own stream,
+  so the work of requests admitted at different times overlaps on the GPU,
+* keeps plans (twiddles, wavenumbers, rho0-weighted coefficients) resident in
+  an LRU cache keyed by the grid, so repeated sizes do not rebuild them,
+* retires finished requests (their memory goes back to the budget) and
+  records each request's latency on the device clock:
+  completion event - start event - arrival time.
+
+Latency therefore covers queueing, admission, the generation of the request's
+input fields on the device, and the projection.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import statistics
+import time
+
+import torch
+
+from . import monc_proj as MP
+from . import workloads as W
+
+
+@dataclasses.dataclass
+class Request:
+    t: float            # arrival time [s] after the start of the run
+    n: int              # nx = ny
+    nz: int
+    seed: int
+
+    @property
+    def points(self) -> int:
+        return self.n * self.n * self.nz
+
+
+@dataclasses.dataclass
+class _Inflight:
+    req: Request
+    slot: int
+    event: torch.cuda.Event
+    nbytes: int
+    tensors: tuple
+
+
+class PlanCache:
+    """LRU cache of resident plans keyed by (n, nz, precision)."""
+
+    def __init__(self, device, capacity=256, grid_fn=W.serving_grid):
+        self.device = device
+        self.capacity = capacity
+        self.grid_fn = grid_fn
+        self.plans = collections.OrderedDict()
+        self.created = 0
+
+    def get(self, n, nz, precision):
+        key = (n, nz, precision)
+        p = self.plans.get(key)
+        if p is not None:
+            self.plans.move_to_end(key)
+            return p
+        p = MP.Plan(self.grid_fn(n, nz), precision, self.device)
+        self.created += 1
+        self.plans[key] = p
+        while len(self.plans) > self.capacity:
+            _, old = self.plans.popitem(last=False)
+            old.close()
+        return p
+
+    def close(self):
+        for p in self.plans.values():
+            p.close()
+        self.plans.clear()
+
+
+def field_bytes(n, nz, elem=4):
+    return elem * n * n * (3 * nz + 1)
+
+
+def make_fields(req: Request, dtype, device, generator):
+    """Synthetic N(0,1) provisional velocities of a request, generated on the
+    device from the request's seed (w's bottom and top faces are zero)."""
+    generator.manual_seed(req.seed)
+    n, nz = req.n, req.nz
+    u = torch.randn((nz, n, n), dtype=dtype, device=device, generator=generator)
+    v = torch.randn((nz, n, n), dtype=dtype, device=device, generator=generator)
+    w = torch.randn((nz + 1, n, n), dtype=dtype, device=device, generator=generator)
+    w[0].zero_()
+    w[nz].zero_()
+    return u, v, w
+
+
+class ProjectionServer:
+    def __init__(self, device=None, hbm_budget=40e9, slots=32, precision="mixed", plan_capacity=256):
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.hbm_budget = float(hbm_budget)
+        self.precision = precision
+        self.dtype = MP.DTYPES[MP.PRECISIONS[precision]]
+        self.streams = [torch.cuda.Stream(self.device) for _ in range(slots)]
+        self.plans = PlanCache(self.device, plan_capacity)
+        self.generator = torch.Generator(device=self.device)
+
+    def request_bytes(self, req, plan):
+        return field_bytes(req.n, req.nz, torch.tensor([], dtype=self.dtype).element_size()) + plan.workspace_bytes
+
+    def prewarm(self, sizes):
+        """Build the plans of the given (n, nz) sizes so they are resident
+        before requests arrive.  Returns the set-up time [s]."""
+        t = time.perf_counter()
+        for n, nz in sizes:
+            self.plans.get(n, nz, self.precision)
+        torch.cuda.synchronize(self.device)
+        return time.perf_counter() - t
+
+    def run(self, requests, keep_outputs=False, time_scale=1.0, prewarm=True):
+        """Serve the requests (sorted by arrival time).  Returns a stats dict;
+        with keep_outputs, stats["outputs"][i] holds request i's (u, v, w).
+        With prewarm, the plans of every size in the stream (the service's
+        size envelope) are built before the first arrival."""
+        reqs = sorted(requests, key=lambda r: r.t)
+        setup_s = 0.0
+        if prewarm:
+            sizes = sorted({(r.n, r.nz) for r in reqs})
+            self.plans.capacity = max(self.plans.capacity, len(sizes))
+            setup_s = self.prewarm(sizes)
+        created_before = self.plans.created
+        pending = collections.deque(enumerate(reqs))
+        queue = collections.deque()
+        inflight: list[_Inflight] = []
+        free_slots = list(range(len(self.streams)))
+        used = 0.0
+        latencies = [None] * len(reqs)
+        outputs = [None] * len(reqs) if keep_outputs else None
+        peak_used = 0.0
+        max_inflight = 0
+        rejected = 0
+        start_ev = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(self.device)
+        t0 = time.perf_counter()
+        start_ev.record(torch.cuda.current_stream(self.device))
+        done_events = [None] * len(reqs)
+        while pending or queue or inflight:
+            now = (time.perf_counter() - t0) / time_scale
+            while pending and pending[0][1].t <= now:
+                queue.append(pending.popleft())
+            # retire finished requests
+            still = []
+            for f in inflight:
+                if f.event.query():
+                    used -= f.nbytes
+                    free_slots.append(f.slot)
+                else:
+                    still.append(f)
+            inflight = still
+            # admit in arrival order while memory and slots allow
+            progressed = False
+            while queue and free_slots:
+                idx, req = queue[0]
+                plan = self.plans.get(req.n, req.nz, self.precision)
+                nbytes = self.request_bytes(req, plan)
+                if nbytes > self.hbm_budget:
+                    queue.popleft()             # can never fit: reject
+                    rejected += 1
+                    continue
+                if used + nbytes > self.hbm_budget and inflight:
+                    break
+                queue.popleft()
+                slot = free_slots.pop()
+                stream = self.streams[slot]
+                with torch.cuda.stream(stream):
+                    u, v, w = make_fields(req, self.dtype, self.device, self.generator)
+                    ws = torch.empty(max(plan.workspace_bytes, 256), dtype=torch.uint8, device=self.device)
+                    MP.monc_proj_solve(plan.handle, u, v, w, u, v, w, None, ws, stream)
+                    ev = torch.cuda.Event(enable_timing=True)
+                    ev.record(stream)
+                for t in (u, v, w, ws):
+                    t.record_stream(stream)
+                done_events[idx] = ev
+                if keep_outputs:
+                    outputs[idx] = (u, v, w)
+                used += nbytes
+                peak_used = max(peak_used, used)
+                inflight.append(_Inflight(req, slot, ev, nbytes, (u, v, w, ws)))
+                max_inflight = max(max_inflight, len(inflight))
+                progressed = True
+            if not progressed:
+                # nothing admitted: wait a little (until the next arrival when idle)
+                wait = 20e-6
+                if pending and not queue and not inflight:
+                    wait = min(1e-3, max(0.0, pending[0][1].t * time_scale - (time.perf_counter() - t0)))
+                if wait > 0:
+                    time.sleep(wait)
+        torch.cuda.synchronize(self.device)
+        wall = time.perf_counter() - t0
+        served = [i for i, e in enumerate(done_events) if e is not None]
+        for i in served:
+            latencies[i] = start_ev.elapsed_time(done_events[i]) / 1e3 - reqs[i].t * time_scale
+        lat = sorted(latencies[i] for i in served)
+        pts = sum(reqs[i].points for i in served)
+        last = max(start_ev.elapsed_time(done_events[i]) / 1e3 for i in served) if served else 0.0
+        first = reqs[0].t * time_scale if reqs else 0.0
+        pct = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))] if lat else None
+        stats = {
+            "requests": len(reqs), "served": len(served), "rejected": rejected,
+            "p50_ms": 1e3 * pct(0.50) if lat else None, "p99_ms": 1e3 * pct(0.99) if lat else None,
+            "max_ms": 1e3 * lat[-1] if lat else None,
+            "mean_ms": 1e3 * statistics.fmean(lat) if lat else None,
+            "points": pts, "mpts_per_s": pts / max(last - first, 1e-9) / 1e6,
+            "wall_s": wall, "peak_hbm_gb": peak_used / 1e9, "hbm_budget_gb": self.hbm_budget / 1e9,
+            "max_inflight": max_inflight, "plans_created_in_loop": self.plans.created - created_before,
+            "plan_setup_s": setup_s, "plans_resident": len(self.plans.plans),
+        }
+        if keep_outputs:
+            stats["outputs"] = outputs
+        return stats
+
+    def close(self):
+        self.plans.close()
+
+
+def requests_from_recipe(count=10000, rate=2000.0, seed=4):
+    return [Request(r["t"], r["n"], r["nz"], r["seed"]) for r in W.serving_requests(count, rate, seed)]
+
+
+def main():
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--requests", type=int, default=10000)
+    ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--budget-gb", type=float, default=40.0)
+    ap.add_argument("--slots", type=int, default=32)
+    a = ap.parse_args()
+    srv = ProjectionServer(hbm_budget=a.budget_gb * 1e9, slots=a.slots)
+    stats = srv.run(requests_from_recipe(a.requests, a.rate))
+    srv.close()
+    print(json.dumps(stats))
+
+
+if __name__ == "__main__":
+    main()

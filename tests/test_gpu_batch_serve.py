@@ -1,0 +1,106 @@
+"""Batched and served projections equal standalone solves of the same inputs."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2009_12849_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _mp():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2009_12849_gb300 import monc_proj
+    return monc_proj
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_batch_equals_individual_solves(prec):
+    mp = _mp()
+    dev = torch.device("cuda", 0)
+    dt = torch.float32 if prec == "mixed" else torch.float64
+    grids = [W.make_grid(n, n, nz, 25.0, 25.0, W.geometric_dz(nz, 10.0, 100.0))
+             for n, nz in ((96, 20), (64, 33), (128, 12), (48, 9), (192, 6), (30, 7))]
+    B = mp.BatchProjector(grids, prec, dev)
+    ins, outs, refs = [], [], []
+    for i, g in enumerate(grids):
+        u, v, w = (torch.tensor(a, dtype=dt, device=dev) for a in W.random_fields(g, 40 + i, True))
+        ins.append((u, v, w))
+        outs.append((torch.empty_like(u), torch.empty_like(v), torch.empty_like(w)))
+        P = mp.Projector.from_grid(g, prec, dev)
+        refs.append([t.clone() for t in P.solve(u, v, w)])
+        torch.cuda.synchronize()
+        P.close()
+    B.solve([(a[0], a[1], a[2], o[0], o[1], o[2]) for a, o in zip(ins, outs)])
+    torch.cuda.synchronize()
+    for o, r in zip(outs, refs):
+        for x, y in zip(o, r):
+            assert torch.equal(x, y)
+    B.close()
+
+
+def test_batch_capturable_in_cuda_graph():
+    mp = _mp()
+    dev = torch.device("cuda", 0)
+    grids = [W.make_grid(n, n, 8, 25.0, 25.0, W.uniform_dz(8, 25.0)) for n in (64, 96, 128)]
+    B = mp.BatchProjector(grids, "mixed", dev)
+    ins = [tuple(torch.tensor(a, dtype=torch.float32, device=dev) for a in W.random_fields(g, 3, False))
+           for g in grids]
+    outs = [tuple(torch.empty_like(t) for t in f) for f in ins]
+    args = [(a[0], a[1], a[2], o[0], o[1], o[2]) for a, o in zip(ins, outs)]
+    B.solve(args)                      # warm-up outside capture
+    torch.cuda.synchronize()
+    ref = [tuple(t.clone() for t in o) for o in outs]
+    for o in outs:
+        for t in o:
+            t.zero_()
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream(dev)
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            B.solve(args, stream=s)
+    graph.replay()
+    torch.cuda.synchronize()
+    for o, r in zip(outs, ref):
+        for x, y in zip(o, r):
+            assert torch.equal(x, y)
+    B.close()
+
+
+def test_served_results_equal_standalone_and_overlap():
+    mp = _mp()
+    from paper_2009_12849_gb300 import serve as S
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(11)
+    reqs = [S.Request(t=0.0002 * i, n=int(rng.choice([64, 96, 120, 128])), nz=int(rng.integers(8, 24)),
+                      seed=500 + i) for i in range(16)]
+    srv = S.ProjectionServer(dev, hbm_budget=8e9, slots=8)
+    stats = srv.run(reqs, keep_outputs=True)
+    assert stats["served"] == len(reqs)
+    assert stats["max_inflight"] > 1            # requests overlapped on the device
+    gen = torch.Generator(device=dev)
+    for i, r in enumerate(sorted(reqs, key=lambda r: r.t)):
+        plan = srv.plans.get(r.n, r.nz, "mixed")
+        u, v, w = S.make_fields(r, torch.float32, dev, gen)
+        ws = torch.empty(max(plan.workspace_bytes, 256), dtype=torch.uint8, device=dev)
+        mp.monc_proj_solve(plan.handle, u, v, w, u, v, w, None, ws)
+        torch.cuda.synchronize()
+        for x, y in zip(stats["outputs"][i], (u, v, w)):
+            assert torch.equal(x, y)
+    srv.close()
+
+
+def test_admission_respects_budget():
+    _mp()
+    from paper_2009_12849_gb300 import serve as S
+    dev = torch.device("cuda", 0)
+    small = [S.Request(t=0.0, n=64, nz=16, seed=i) for i in range(6)]
+    one = S.field_bytes(64, 16) + 1
+    srv = S.ProjectionServer(dev, hbm_budget=2.2 * (one + 64 * 64 * 16 * 40), slots=8)
+    huge = S.Request(t=0.0, n=512, nz=192, seed=99)
+    stats = srv.run(small + [huge])
+    assert stats["rejected"] == 1 and stats["served"] == 6
+    assert stats["max_inflight"] <= 2
+    assert stats["peak_hbm_gb"] <= stats["hbm_budget_gb"]
+    srv.close()

@@ -31,3 +31,10 @@ def test_serving_and_batch_recipes():
     inst = W.batch_instances(64)
     assert len(inst) == 64
     assert {g.nx for g, _ in inst} <= {64, 96, 128, 192, 256}
+
+
+def test_serving_request_objects():
+    from paper_2009_12849_gb300 import serve as S
+    reqs = S.requests_from_recipe(50, 2000.0, 4)
+    assert len(reqs) == 50 and all(r.points == r.n * r.n * r.nz for r in reqs)
+    assert S.field_bytes(10, 3) == 4 * 10 * 10 * 10
