@@ -581,10 +581,61 @@ __device__ __forceinline__ InvColField<R> inv_col_field(const ProjParams& p, int
     return r;
 }
 
+// Compile-time lengths: task = (level, tile, kind); kind 0 reads the p^ tile
+// and writes every field derived from it (x-gradient with ex, y-gradient,
+// phi if requested; the re-reads of the tile hit L2), kind 1 transforms gz^.
+template <typename R, int NY>
+__device__ __forceinline__ void inv_cols_ct_task(const ProjParams& p, int k, int kx0, int f, cplx<R>* buf) {
+    using C = cplx<R>;
+    const InvColField<R> fd = inv_col_field<R>(p, f, k);
+    const int nxh = p.nxh, nxp = p.nxp, ny = p.ny;
+    const C* src = fd.src + (size_t)k * ny * nxp;
+    const C* ey = fd.ey;
+    auto load = [&](int c, int j) -> C {
+        const int kx = kx0 + c;
+        if (kx >= nxh) return cmk<R>((R)0, (R)0);
+        const C v = src[(size_t)j * nxp + kx];
+        return ey ? cmul(v, ey[j]) : v;
+    };
+    ct_first<R, NY, 1, true>(buf, p.tw_cols, p.bs_col, load);
+    CtMid<R, NY, StageInfo<R, NY, 1>::NEXT, 1>::run(buf, p.tw_cols, p.bs_col, ctab<R>(p.twy));
+    const C* ex = ctab<R>(p.ex);
+    const bool mul_ex = fd.ex;
+    C* dst = fd.dst + (size_t)k * ny * nxp;
+    auto store = [&](int c, int q, const C* x, int ns) {
+        const int kx = kx0 + c;
+        if (kx >= nxh) return;
+        constexpr int RAD = StageInfo<R, NY, LastNs<R, NY>::value>::RAD;
+        const C e = mul_ex ? ex[kx] : cmk<R>((R)1, (R)0);
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) dst[(size_t)(q + r * ns) * nxp + kx] = mul_ex ? cmul(x[r], e) : x[r];
+    };
+    ct_last<R, NY, 1, true>(buf, p.tw_cols, p.bs_col, ctab<R>(p.twy), store);
+}
+
 template <typename R, int NY>
 __global__ void __launch_bounds__(512) k_inv_cols(ProjParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using C = cplx<R>;
+    if constexpr (NY > 0) {
+        const int kind = blockIdx.x & 1;
+        const int task = blockIdx.x >> 1;
+        const int k = task / p.ntiles;
+        const int kx0 = (task - k * p.ntiles) * p.tw_cols;
+        C* buf = (C*)smem_raw;
+        if (kind == 0) {
+            inv_cols_ct_task<R, NY>(p, k, kx0, 0, buf);
+            __syncthreads();
+            inv_cols_ct_task<R, NY>(p, k, kx0, 1, buf);
+            if (p.nch == 4) {
+                __syncthreads();
+                inv_cols_ct_task<R, NY>(p, k, kx0, 3, buf);
+            }
+        } else if (k > 0) {
+            inv_cols_ct_task<R, NY>(p, k, kx0, 2, buf);
+        }
+        return;
+    }
     const int nf = p.nch;
     const int f = blockIdx.x % nf;
     const int task = blockIdx.x / nf;

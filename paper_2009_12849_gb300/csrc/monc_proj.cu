@@ -40,6 +40,7 @@ struct monc_proj_plan_s {
     int nsm;                              // SMs of the plan's device (persistent grids)
     bool persist_cols;                    // compile-time lengths: persistent cp.async column kernels
     bool ct_rows;                         // compile-time length along x
+    bool ct_cols;                         // compile-time length along y
     bool fused;                           // square compile-time grid: fused persistent kernels
     int ring;                             // levels in the L2 rings of the fused kernels
     int lag;                              // producer/consumer lag of the fused kernels
@@ -139,6 +140,12 @@ FftFactors factorize(int n, int maxrad) {
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// The persistent cp.async inverse-column kernel is opt-in (MONC_PROJ_PERSIST_COLS=1).
+bool persist_cols_enabled() {
+    const char* e = std::getenv("MONC_PROJ_PERSIST_COLS");
+    return e && e[0] == '1';
+}
 
 // The fused persistent kernels are opt-in (MONC_PROJ_FUSED=1 in the
 // environment): on GB300 they measured slower than the split kernels.
@@ -290,7 +297,7 @@ int launch_solve(monc_proj_plan_s* p, const ProjParams& q, cudaStream_t st) {
     } else {
         const SolveKernels ks = pick_kernels<R>(p);
         const int n_fcols = nz * p->ntiles;
-    const int n_icols = nz * p->ntiles * (p->persist_cols ? 2 : q.nch);
+    const int n_icols = nz * p->ntiles * ((p->persist_cols || p->ct_cols) ? 2 : q.nch);
         const int n_irows = nz * q.nrb_inv * (p->ct_rows ? q.nch : 1);
         pm.start(0, st);
         ks.fwd_rows<<<nz * p->nrb_fwd, p->thr_fwd_rows, p->smem_fwd_rows, st>>>(q);
@@ -523,11 +530,12 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     p->thr_cols = cty ? threads_for(tw * ny, E) : 256;
     p->smem_cols = (size_t)(cty ? 1 : 2) * tw * p->bs_col * csz;
     p->smem_fcols = p->smem_cols;
-    // compile-time lengths run the persistent inverse column kernel: two
-    // input stages of ny x tw values plus the FFT buffer
-    p->persist_cols = cty;
-    if (cty) p->smem_cols = ((size_t)2 * ny * tw + (size_t)tw * p->bs_col) * csz;
+    // the persistent inverse column kernel (opt-in) holds two input stages
+    // of ny x tw values plus the FFT buffer
+    p->persist_cols = cty && persist_cols_enabled();
+    if (p->persist_cols) p->smem_cols = ((size_t)2 * ny * tw + (size_t)tw * p->bs_col) * csz;
     p->ct_rows = ctx;
+    p->ct_cols = cty;
     // inverse row tasks: pairs of rows, one complex transform per channel and
     // row pair; index 0 without phi output (3 channels), 1 with (4 channels)
     for (int idx = 0; idx < 2; ++idx) {
