@@ -133,9 +133,16 @@ typedef struct {
 int monc_proj_batch_workspace_size(const monc_proj_plan_t* plans, int count, size_t* bytes);
 
 /*
- * `count` independent projections (plans may differ in size and precision)
- * enqueued together on one stream as one fused launch per phase; the result
- * of each equals that of monc_proj_solve on the same inputs.
+ * `count` independent projections (plans may differ in size and precision),
+ * ordered after the work already on `stream` and before work enqueued on it
+ * afterwards.  Inside, the instances run concurrently on an internal pool of
+ * streams (largest first), so uneven small problems share the GPU; each
+ * result equals that of monc_proj_solve on the same inputs.  Instance i uses
+ * the workspace slice that starts at the sum of align256(workspace_size) of
+ * instances 0..i-1.  The call only enqueues work; its fork and join are
+ * events, so a caller may capture it into a CUDA graph on `stream`.  Errors:
+ * EINVAL for a NULL plan or field pointer or a short workspace; the first
+ * failing instance's status otherwise.
  */
 int monc_proj_solve_batch(const monc_proj_plan_t* plans, const monc_proj_fields* fields,
                           int count, void* workspace, size_t workspace_bytes, void* stream);

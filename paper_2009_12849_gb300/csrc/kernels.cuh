@@ -454,8 +454,8 @@ __device__ __forceinline__ void tridiag_column_mixed64(const ProjParams& p, size
 // memory); the back substitution recomputes each segment's forward values in
 // registers from its checkpoint, re-reading D'.  D' is read twice, but y and
 // 1/e never travel to DRAM and back.
-constexpr int kTriSeg = 16;
-constexpr int kTriMaxSeg = 64;               // nz <= kTriSeg * kTriMaxSeg
+constexpr int kTriSeg = 8;
+constexpr int kTriMaxSeg = 128;              // nz <= kTriSeg * kTriMaxSeg
 
 __device__ __forceinline__ void tridiag_column_ckpt32(const ProjParams& p, size_t base, float lam) {
     using C = float2;
@@ -485,7 +485,7 @@ __device__ __forceinline__ void tridiag_column_ckpt32(const ProjParams& p, size_
                 const float ak = vc.a[k];
                 const float m = ak * g;
                 const float e = lam * vc.s[k] - vc.c[k] - ak * m;
-                g = 1.f / e;
+                g = __frcp_rn(e);
                 y = make_float2(d[i].x - m * y.x, d[i].y - m * y.y);
             }
         }
@@ -508,7 +508,7 @@ __device__ __forceinline__ void tridiag_column_ckpt32(const ProjParams& p, size_
                 const float ak = vc.a[k];
                 const float m = ak * gg;
                 const float e = lam * vc.s[k] - vc.c[k] - ak * m;
-                gg = 1.f / e;
+                gg = __frcp_rn(e);
                 yy = make_float2(d[i].x - m * yy.x, d[i].y - m * yy.y);
             }
             ys[i] = yy;
@@ -534,7 +534,7 @@ __device__ __forceinline__ void tridiag_column_ckpt32(const ProjParams& p, size_
 }
 
 template <typename R>
-__global__ void __launch_bounds__(128) k_tridiag(ProjParams p) {
+__global__ void __launch_bounds__(128, 8) k_tridiag(ProjParams p) {
     const int nxw = (p.nxh + 31) & ~31;
     const long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int ky = (int)(col / nxw);
