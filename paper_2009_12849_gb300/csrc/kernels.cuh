@@ -533,13 +533,18 @@ __device__ __forceinline__ void tridiag_column_ckpt32(const ProjParams& p, size_
     }
 }
 
+// Rows are taken in the order ky = 0, ny-1, 1, ny-2, ...: the columns of
+// small |lambda| (the FP64 ones of a mixed plan, limited by the FP64 rate) sit at
+// both ends of the ky range and so start in the first wave of blocks, where
+// they overlap the FP32 columns instead of forming a tail.
 template <typename R>
 __global__ void __launch_bounds__(128, 8) k_tridiag(ProjParams p) {
     const int nxw = (p.nxh + 31) & ~31;
     const long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int ky = (int)(col / nxw);
-    const int kx = (int)(col - (long long)ky * nxw);
-    if (ky >= p.ny || kx >= p.nxh) return;
+    const int r = (int)(col / nxw);
+    const int kx = (int)(col - (long long)r * nxw);
+    if (r >= p.ny || kx >= p.nxh) return;
+    const int ky = (r & 1) ? p.ny - 1 - (r >> 1) : (r >> 1);
     const size_t base = (size_t)ky * p.nxp + kx;
     const double lam = p.lamx[kx] + p.lamy[ky];
     const bool mean = (kx == 0 && ky == 0);
