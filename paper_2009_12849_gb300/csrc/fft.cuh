@@ -203,11 +203,15 @@ __device__ cplx<R>* fft_batch(cplx<R>* a, cplx<R>* b, int nb, int bstride,
 // and the outputs overwrite the inputs in the single shared buffer.  The
 // caller sizes the block so that blockDim.x * E >= nb * N.
 // ---------------------------------------------------------------------------
-template <typename R> struct ElemsPerThread { static constexpr int value = sizeof(R) == 4 ? 32 : 16; };
+// Largest radix of the compile-time plans, which is also the number of
+// elements a thread holds in a stage (FP32, FP64).
+constexpr int kMaxRadixF32 = 32;
+constexpr int kMaxRadixF64 = 16;
+template <typename R> struct ElemsPerThread { static constexpr int value = sizeof(R) == 4 ? kMaxRadixF32 : kMaxRadixF64; };
 
 // Radix of the next stage for the remaining length M (largest first).
 template <typename R, int M> struct NextRadix {
-    static constexpr int maxr = sizeof(R) == 4 ? 32 : 16;
+    static constexpr int maxr = ElemsPerThread<R>::value;
     static constexpr int value = (maxr >= 32 && M % 32 == 0) ? 32 : (M % 16 == 0) ? 16 : (M % 8 == 0) ? 8
                                : (M % 4 == 0) ? 4 : (M % 2 == 0) ? 2 : (M % 5 == 0) ? 5 : 3;
 };
@@ -217,7 +221,7 @@ template <typename R, int N> constexpr int stage_index_impl(int target) {
     int ns = 1, s = 0;
     while (ns < target) {
         const int m = N / ns;
-        const int maxr = sizeof(R) == 4 ? 32 : 16;
+        const int maxr = ElemsPerThread<R>::value;
         const int rad = (maxr >= 32 && m % 32 == 0) ? 32 : (m % 16 == 0) ? 16 : (m % 8 == 0) ? 8
                       : (m % 4 == 0) ? 4 : (m % 2 == 0) ? 2 : (m % 5 == 0) ? 5 : 3;
         ns *= rad;
@@ -307,7 +311,7 @@ template <typename R, int N> constexpr int last_stage_ns_impl() {
     int ns = 1;
     while (ns < N) {
         const int m = N / ns;
-        const int maxr = sizeof(R) == 4 ? 32 : 16;
+        const int maxr = ElemsPerThread<R>::value;
         const int rad = (maxr >= 32 && m % 32 == 0) ? 32 : (m % 16 == 0) ? 16 : (m % 8 == 0) ? 8
                       : (m % 4 == 0) ? 4 : (m % 2 == 0) ? 2 : (m % 5 == 0) ? 5 : 3;
         if (ns * rad == N) return ns;

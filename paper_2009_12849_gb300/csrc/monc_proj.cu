@@ -95,6 +95,14 @@ PhaseMarks begin_marks(monc_proj_plan_s* p) {
 
 constexpr size_t kSmemMax = 200 * 1024;
 constexpr size_t kSmemPersist = 220 * 1024;
+// Threads of a compile-time-length task (a thread holds E elements of a
+// stage): row tasks of one warp (one complex transform at nx = 1024) measured
+// fastest, 1.47 ms for the inverse rows of 1024^2 x 256 against 1.63 ms with
+// 256 threads; column tiles of 256 threads (8 columns of 1024, 64-byte row
+// segments) beat both narrower and wider tiles.
+constexpr int kRowTaskThreads = 32;
+constexpr int kColTaskThreads = 256;
+
 // Mixed plans: a3 runs in FP64 for columns with |lambda| < kFp64Fraction * v_max.
 // The FP32 sweep's contribution to the divergence residual was measured (in an
 // FP32 emulation of the sweep) at about 7e-8 above this bound and grows to
@@ -147,8 +155,15 @@ bool persist_cols_enabled() {
     return e && e[0] == '1';
 }
 
+int env_int(const char* name, int dflt) {
+    const char* e = std::getenv(name);
+    return (e && *e) ? std::max(1, std::atoi(e)) : dflt;
+}
+
 // The fused persistent kernels are opt-in (MONC_PROJ_FUSED=1 in the
-// environment): on GB300 they measured slower than the split kernels.
+// environment; MONC_PROJ_FUSED_LAG and MONC_PROJ_FUSED_RING set the
+// producer/consumer lag and the ring depth in levels): on GB300 they measured
+// slower than the split kernels at every lag and ring depth tried.
 bool fused_disabled() {
     const char* e = std::getenv("MONC_PROJ_FUSED");
     return !(e && e[0] == '1');
@@ -297,7 +312,7 @@ int launch_solve(monc_proj_plan_s* p, const ProjParams& q, cudaStream_t st) {
     } else {
         const SolveKernels ks = pick_kernels<R>(p);
         const int n_fcols = nz * p->ntiles;
-    const int n_icols = nz * p->ntiles * ((p->persist_cols || p->ct_cols) ? 2 : q.nch);
+        const int n_icols = nz * p->ntiles * ((p->persist_cols || p->ct_cols) ? 2 : q.nch);
         const int n_irows = nz * q.nrb_inv * (p->ct_rows ? q.nch : 1);
         pm.start(0, st);
         ks.fwd_rows<<<nz * p->nrb_fwd, p->thr_fwd_rows, p->smem_fwd_rows, st>>>(q);
@@ -406,8 +421,8 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     p->nx = nx; p->ny = ny; p->nz = nz; p->dx = dx; p->dy = dy; p->precision = precision;
     p->nxh = nx / 2 + 1;
     p->nxp = (p->nxh + 3) & ~3;
-    p->fx = factorize(nx, precision == MONC_PROJ_FP64 ? 16 : 32);
-    p->fy = factorize(ny, precision == MONC_PROJ_FP64 ? 16 : 32);
+    p->fx = factorize(nx, precision == MONC_PROJ_FP64 ? kMaxRadixF64 : kMaxRadixF32);
+    p->fy = factorize(ny, precision == MONC_PROJ_FP64 ? kMaxRadixF64 : kMaxRadixF32);
 
     const bool fp64 = precision == MONC_PROJ_FP64;
     const size_t csz = fp64 ? 16 : 8;
@@ -505,9 +520,10 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     blob.resize(blob.size() + 256, 0);
 
     // ---- task shapes.  Compile-time lengths: one shared buffer, blocks of
-    // about 256 threads x E elements (E = 32 FP32, 16 FP64 values per thread).
-    // Run-time lengths: two buffers (ping-pong) within ~96 KB, 256 threads.
-    const int E = fp64 ? 16 : 32;
+    // kRowTaskThreads (rows) or kColTaskThreads (column tiles) threads x E
+    // elements (E = the largest radix: 32 FP32, 16 FP64).  Run-time lengths:
+    // two buffers (ping-pong) within ~96 KB, 256 threads.
+    const int E = fp64 ? kMaxRadixF64 : kMaxRadixF32;
     const bool ctx = ct_length(nx, fp64), cty = ct_length(ny, fp64);
     p->bs_row = spad_len(nx);
     // column tiles: a pitch of 4 (mod 16) complex elements spreads the
@@ -515,14 +531,14 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     p->bs_col = spad_len(ny);
     while (p->bs_col % 16 != 4) ++p->bs_col;
     const size_t budget = 96 * 1024;
-    int npair = ctx ? std::max(1, std::min(16, 256 * E / nx))
+    int npair = ctx ? std::max(1, std::min(16, kRowTaskThreads * E / nx))
                     : (int)std::max<size_t>(1, std::min<size_t>(8, budget / (2 * (size_t)p->bs_row * csz)));
     npair = std::min(npair, (ny + 1) / 2);
     p->rows_fwd = 2 * npair;
     p->nrb_fwd = (ny + p->rows_fwd - 1) / p->rows_fwd;
     p->thr_fwd_rows = ctx ? threads_for(npair * nx, E) : 256;
     p->smem_fwd_rows = (size_t)(ctx ? 1 : 2) * npair * p->bs_row * csz;
-    int tw = cty ? std::max(1, std::min(32, 256 * E / ny))
+    int tw = cty ? std::max(1, std::min(32, kColTaskThreads * E / ny))
                  : (int)std::max<size_t>(1, std::min<size_t>(8, budget / (2 * (size_t)p->bs_col * csz)));
     tw = std::min(tw, p->nxh);
     p->tw_cols = tw;
@@ -548,7 +564,7 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
         p->smem_inv_rows[idx] = (size_t)(ctx ? 1 : 2) * np * p->bs_row * csz;
         if (ctx) {
             // one channel per task: rows_inv rows = rows_inv/2 transforms
-            int npr = std::max(1, std::min({16, 256 * E / nx, (ny + 1) / 2}));
+            int npr = std::max(1, std::min({16, kRowTaskThreads * E / nx, (ny + 1) / 2}));
             p->rows_inv[idx] = 2 * npr;
             p->thr_inv_rows[idx] = threads_for(npr * nx, E);
             p->smem_inv_rows[idx] = (size_t)npr * p->bs_row * csz;
@@ -568,8 +584,8 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     }
     // consumers trail producers by `lag` levels; a ring of lag + 3 levels
     // lets producers run ahead without waiting for slots
-    p->lag = std::min(nz, 3);
-    if (p->fused) p->ring = std::min(nz, p->lag + 3);
+    p->lag = std::min(nz, env_int("MONC_PROJ_FUSED_LAG", 3));
+    if (p->fused) p->ring = std::min(nz, std::max(p->lag + 1, env_int("MONC_PROJ_FUSED_RING", p->lag + 3)));
 
     // ---- workspace layout
     const size_t L = (size_t)nz * ny * p->nxp;
