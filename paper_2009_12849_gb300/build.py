@@ -47,6 +47,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
               "-I", os.path.join(ROOT, "include")]
     if verbose:
         common.append("-Xptxas=-v")
+    common += os.environ.get("MONC_PROJ_NVCC_EXTRA", "").split()
     procs = []
     objs = []
     for src in SOURCES:

@@ -412,4 +412,50 @@ __device__ __forceinline__ void ct_last(const cplx<R>* buf, int nb, int bstride,
     }
 }
 
+// Last stage for an output buffer that aliases the input: every thread
+// computes its butterflies into registers, the block synchronises, then the
+// results go to store(b, q, x, NS).
+template <typename R, int N, int S, bool BFAST, class Store>
+__device__ __forceinline__ void ct_last_sync(const cplx<R>* buf, int nb, int bstride, const cplx<R>* __restrict__ tws,
+                                             Store&& store) {
+    constexpr int NS = LastNs<R, N>::value;
+    const cplx<R>* __restrict__ tw = tws + StageIndex<R, N, NS>::value * N;
+    using SI = StageInfo<R, N, NS>;
+    static_assert(SI::LAST, "last stage");
+    constexpr int RAD = SI::RAD, NQ = SI::NQ;
+    constexpr int E = ElemsPerThread<R>::value;
+    constexpr int NB = (E + RAD - 1) / RAD;
+    const int total = NQ * nb;
+    cplx<R> x[NB][RAD];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int t = threadIdx.x + i * blockDim.x;
+        if (t < total) {
+            int b, q;
+            bfly_map<BFAST, NQ>(t, nb, b, q);
+            const cplx<R>* src = buf + b * bstride;
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) x[i][r] = src[spad(q + r * NQ)];
+            if (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < RAD; ++r) {
+                    const cplx<R> wv = __ldg(&tw[r * NS + q]);
+                    x[i][r] = (S < 0) ? cmul(x[i][r], wv) : cmulc(x[i][r], wv);
+                }
+            }
+            RegFFT<R, RAD, S>::run(x[i]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int t = threadIdx.x + i * blockDim.x;
+        if (t < total) {
+            int b, q;
+            bfly_map<BFAST, NQ>(t, nb, b, q);
+            store(b, q, x[i], NS);
+        }
+    }
+}
+
 }  // namespace mp

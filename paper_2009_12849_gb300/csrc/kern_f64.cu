@@ -12,4 +12,5 @@ template <> KernelFn pick_inv_cols_persist<double>(int n) { MP_PICK_F64(k_cols_p
 template <> KernelFn pick_fwd_fused<double>(int n) { MP_PICK_F64(k_fwd_fused, nullptr) }
 template <> KernelFn pick_inv_fused<double>(int n) { MP_PICK_F64(k_inv_fused, nullptr) }
 template <> KernelFn pick_tridiag<double>() { return k_tridiag<double>; }
+template <> ColsTmaFn pick_cols_tma<double>(int, bool) { return nullptr; }
 }  // namespace mp

@@ -13,6 +13,8 @@
 #include <new>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "pickers.h"
 
 using namespace mp;
@@ -42,6 +44,8 @@ struct monc_proj_plan_s {
     bool ct_rows;                         // compile-time length along x
     bool ct_cols;                         // compile-time length along y
     bool fused;                           // square compile-time grid: fused persistent kernels
+    bool tma_cols;                        // FP32 compile-time column lengths: TMA-staged column kernels
+    size_t smem_tma;                      // their dynamic shared memory (two tile buffers)
     int ring;                             // levels in the L2 rings of the fused kernels
     int lag;                              // producer/consumer lag of the fused kernels
     int grid_fwd_fused, grid_inv_fused;
@@ -284,6 +288,71 @@ template <typename R> SolveKernels pick_kernels(const monc_proj_plan_s* p) {
                         pick_k_inv_rows<R>(nx)};
 }
 
+// ---------------------------------------------------------------------------
+// Tensor maps of the TMA column kernels.  cuTensorMapEncodeTiled comes from
+// the driver through the runtime's entry-point query, so the library needs no
+// link-time dependency on the driver API.
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return (PFN_cuTensorMapEncodeTiled_v12000)f;
+    }();
+    return fn;
+}
+
+// The TMA column kernels are opt-in (MONC_PROJ_TMA=1): they measured slower
+// than the register-staged column kernels on GB300.
+bool tma_enabled() {
+    const char* e = std::getenv("MONC_PROJ_TMA");
+    return e && e[0] == '1';
+}
+
+// 2D view of a spectral array [nz*ny rows][nxh valid columns], row pitch nxp
+// complex values, boxes of tw columns x min(ny, 256) rows; columns at and past
+// nxh read as zero and are not written.
+bool encode_cols_map(const monc_proj_plan_s* p, CUtensorMap* m, const void* base) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc || !base) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)p->nxh, (cuuint64_t)p->nz * (cuuint64_t)p->ny};
+    const cuuint64_t strides[1] = {(cuuint64_t)p->nxp * 8};
+    const cuuint32_t box[2] = {(cuuint32_t)p->tw_cols, (cuuint32_t)std::min(p->ny, 256)};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_64B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Forward (T -> S) or inverse (S, G -> Tp, Tgy, Tgz[, Tphi]) column phase on
+// the TMA kernels; false (nothing launched) if a map cannot be encoded.
+template <typename R>
+bool launch_cols_tma(const monc_proj_plan_s* p, const ProjParams& q, bool inv, cudaStream_t st) {
+    const ColsTmaFn fn = pick_cols_tma<R>(p->ny, inv);
+    if (!fn) return false;
+    ColMaps m;
+    std::memset(&m, 0, sizeof(m));
+    bool ok;
+    if (!inv) {
+        ok = encode_cols_map(p, &m.src[0], q.T) && encode_cols_map(p, &m.dst[0], q.S);
+    } else {
+        ok = encode_cols_map(p, &m.src[0], q.S) && encode_cols_map(p, &m.src[1], q.G) &&
+             encode_cols_map(p, &m.dst[0], q.Tp) && encode_cols_map(p, &m.dst[1], q.Tgy) &&
+             encode_cols_map(p, &m.dst[2], q.Tgz) && (q.nch < 4 || encode_cols_map(p, &m.dst[3], q.Tphi));
+    }
+    if (!ok) return false;
+    const long long items = (long long)p->nz * p->ntiles * (inv ? q.nch : 1);
+    const int grid = (int)std::min<long long>(items, p->nsm);
+    fn<<<grid, p->thr_cols, p->smem_tma, st>>>(q, m);
+    return true;
+}
+
 template <typename R>
 int launch_solve(monc_proj_plan_s* p, const ProjParams& q, cudaStream_t st) {
     const int nz = p->nz;
@@ -310,7 +379,8 @@ int launch_solve(monc_proj_plan_s* p, const ProjParams& q, cudaStream_t st) {
         ks.fwd_rows<<<nz * p->nrb_fwd, p->thr_fwd_rows, p->smem_fwd_rows, st>>>(q);
         pm.end(0, st);
         pm.start(1, st);
-        ks.fwd_cols<<<n_fcols, p->thr_cols, p->smem_fcols, st>>>(q);
+        if (!(p->tma_cols && launch_cols_tma<R>(p, q, false, st)))
+            ks.fwd_cols<<<n_fcols, p->thr_cols, p->smem_fcols, st>>>(q);
         pm.end(1, st);
         pm.start(2, st);
         pick_tridiag<R>()<<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(q);
@@ -320,7 +390,8 @@ int launch_solve(monc_proj_plan_s* p, const ProjParams& q, cudaStream_t st) {
             cudaGetLastError();
             return MONC_PROJ_ECUDA;
         }
-        ks.inv_cols<<<p->persist_cols ? std::min(n_icols, p->nsm) : n_icols, p->thr_cols, p->smem_cols, st>>>(q);
+        if (!(p->tma_cols && launch_cols_tma<R>(p, q, true, st)))
+            ks.inv_cols<<<p->persist_cols ? std::min(n_icols, p->nsm) : n_icols, p->thr_cols, p->smem_cols, st>>>(q);
         pm.end(3, st);
         pm.start(4, st);
         ks.inv_rows<<<n_irows, p->thr_inv_rows[inv_idx], p->smem_inv_rows[inv_idx], st>>>(q);
@@ -343,6 +414,16 @@ int set_kernel_attrs(const monc_proj_plan_s* p) {
         std::max(p->smem_inv_rows[0], p->smem_inv_rows[1]) > lim_rows)
         return MONC_PROJ_EUNSUPPORTED;
     const SolveKernels ks = pick_kernels<R>(p);
+    if (p->tma_cols) {
+        for (int inv = 0; inv < 2; ++inv) {
+            const ColsTmaFn f = pick_cols_tma<R>(p->ny, inv != 0);
+            if (f && cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)p->smem_tma) != cudaSuccess) {
+                cudaGetLastError();
+                return MONC_PROJ_ECUDA;
+            }
+        }
+    }
     const KernelFn fns[] = {ks.fwd_rows, ks.fwd_cols, ks.inv_cols, ks.inv_rows};
     const size_t lims[] = {kSmemMax, kSmemMax, lim_cols, lim_rows};
     for (int i = 0; i < 4; ++i) {
@@ -545,6 +626,11 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     // the persistent inverse column kernel (opt-in) holds two input stages
     // of ny x tw values plus the FFT buffer
     p->persist_cols = cty && persist_cols_enabled();
+    // TMA column kernels (opt-in): FP32 compile-time lengths (rows of tw >= 2
+    // complex values, a multiple of 16 bytes)
+    p->smem_tma = (size_t)2 * tw * p->bs_col * csz + 128 + 32;    // + alignment slack, mbarriers
+    p->tma_cols = !fp64 && cty && !p->persist_cols && (tw * csz) % 16 == 0 && p->smem_tma <= kSmemMax &&
+                  tma_enabled() && tmap_encoder() != nullptr;
     if (p->persist_cols) p->smem_cols = ((size_t)2 * ny * tw + (size_t)tw * p->bs_col) * csz;
     p->ct_rows = ctx;
     p->ct_cols = cty;

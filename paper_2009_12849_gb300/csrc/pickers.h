@@ -6,11 +6,12 @@
 // 1024; FP64: 64, 128, 256, 1024) get their own instantiation; every other
 // 2^a 3^b 5^c length runs the run-time plan (template argument 0).
 #pragma once
-#include "kernels.cuh"
+#include "tma.cuh"
 
 namespace mp {
 
 using KernelFn = void (*)(ProjParams);
+using ColsTmaFn = void (*)(ProjParams, ColMaps);
 
 template <typename R> KernelFn pick_k_fwd_rows(int n);
 template <typename R> KernelFn pick_k_inv_rows(int n);
@@ -21,6 +22,7 @@ template <typename R> KernelFn pick_inv_cols_persist(int n);
 template <typename R> KernelFn pick_fwd_fused(int n);
 template <typename R> KernelFn pick_inv_fused(int n);
 template <typename R> KernelFn pick_tridiag();
+template <typename R> ColsTmaFn pick_cols_tma(int n, bool inv);  // nullptr if none
 
 }  // namespace mp
 

@@ -137,3 +137,15 @@ def test_invalid_arguments_rejected():
     rc = mp.load_library().monc_proj_solve(None, None, None, None, None, None, None, None, None, None)
     assert rc == mp.MONC_PROJ_EINVAL
     P.close()
+
+
+@pytest.mark.parametrize("shape", [(128, 192, 8), (256, 512, 3), (96, 1024, 4)])
+def test_opt_in_kernel_variants(shape, monkeypatch):
+    """The opt-in column kernels (TMA-staged tiles; persistent cp.async
+    tiles) give the same projection as the default kernels."""
+    nx, ny, nz = shape
+    g = W.make_grid(nx, ny, nz, 25.0, 20.0, W.geometric_dz(nz, 10.0, 100.0))
+    for var in ("MONC_PROJ_TMA", "MONC_PROJ_PERSIST_COLS"):
+        monkeypatch.setenv(var, "1")
+        check_case(g, 5, True, "mixed")
+        monkeypatch.delenv(var)
