@@ -9,7 +9,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmonc_proj.so")
-SOURCES = ["monc_proj.cu", "kern_f32_rows.cu", "kern_f32_cols.cu", "kern_f32_fused.cu", "kern_f64.cu"]
+# (source, extra defines, object name): kern_f32_ext.cu is compiled once per
+# group of extended FP32 lengths and part (rows / columns)
+SOURCES = [(f, [], os.path.splitext(f)[0]) for f in
+           ("monc_proj.cu", "kern_f32_rows.cu", "kern_f32_cols.cu", "kern_f32_fused.cu", "kern_f64.cu")]
+SOURCES += [("kern_f32_ext.cu", [f"-DMP_EXT_GROUP={g}", f"-DMP_EXT_PART={part}"], f"kern_f32_ext{g}_{part}")
+            for g in (1, 2, 3, 4) for part in (0, 1)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -50,11 +55,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
     common += os.environ.get("MONC_PROJ_NVCC_EXTRA", "").split()
     procs = []
     objs = []
-    for src in SOURCES:
-        obj = os.path.join(objdir, os.path.splitext(src)[0] + ".o")
+    for src, defs, name in SOURCES:
+        obj = os.path.join(objdir, name + ".o")
         objs.append(obj)
-        procs.append((src, subprocess.Popen(common + ["-c", os.path.join(CSRC, src), "-o", obj],
-                                            stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
+        procs.append((name, subprocess.Popen(common + defs + ["-c", os.path.join(CSRC, src), "-o", obj],
+                                             stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
     errors = []
     for src, pr in procs:
         out, _ = pr.communicate()

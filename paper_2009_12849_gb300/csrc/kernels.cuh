@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(512) k_fwd_rows(ProjParams p) {
     const R idx = (R)p.idx, idy = (R)p.idy;
 
     const C* res;
-    if constexpr (NX > 0 && sizeof(R) == 4) {
+    if constexpr (NX > 0 && NX % 4 == 0 && sizeof(R) == 4) {
         // FP32, compile-time length: every thread takes groups of 4 adjacent
         // cells of a row and loads them as float4 (u, v, v of the row below,
         // w below and above), 4 groups in flight per thread.

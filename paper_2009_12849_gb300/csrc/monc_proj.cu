@@ -272,8 +272,11 @@ ProjParams make_params(const monc_proj_plan_s* p, const void* u, const void* v, 
 // ---------------------------------------------------------------------------
 bool ct_length(int n, bool fp64) {
     if (fp64) return n == 64 || n == 128 || n == 256 || n == 1024;
-    return n == 64 || n == 96 || n == 128 || n == 192 || n == 256 || n == 512 || n == 1024;
+    return ct_length_f32(n);
 }
+
+// Lengths that also have the opt-in kernel variants (persistent, TMA, fused).
+bool ct_core_length(int n, bool fp64) { return fp64 ? ct_length(n, true) : ct_core_f32(n); }
 
 
 struct SolveKernels {
@@ -625,11 +628,11 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     p->smem_fcols = p->smem_cols;
     // the persistent inverse column kernel (opt-in) holds two input stages
     // of ny x tw values plus the FFT buffer
-    p->persist_cols = cty && persist_cols_enabled();
+    p->persist_cols = cty && ct_core_length(ny, fp64) && persist_cols_enabled();
     // TMA column kernels (opt-in): FP32 compile-time lengths (rows of tw >= 2
     // complex values, a multiple of 16 bytes)
     p->smem_tma = (size_t)2 * tw * p->bs_col * csz + 128 + 32;    // + alignment slack, mbarriers
-    p->tma_cols = !fp64 && cty && !p->persist_cols && (tw * csz) % 16 == 0 && p->smem_tma <= kSmemMax &&
+    p->tma_cols = !fp64 && cty && ct_core_length(ny, fp64) && !p->persist_cols && (tw * csz) % 16 == 0 && p->smem_tma <= kSmemMax &&
                   tma_enabled() && tmap_encoder() != nullptr;
     if (p->persist_cols) p->smem_cols = ((size_t)2 * ny * tw + (size_t)tw * p->bs_col) * csz;
     p->ct_rows = ctx;
@@ -655,7 +658,7 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
 
     // fused persistent kernels for square compile-time grids: one block size
     // and shared-memory size for both task kinds of each kernel
-    p->fused = ctx && cty && nx == ny && !fused_disabled();
+    p->fused = ctx && cty && nx == ny && ct_core_length(nx, fp64) && !fused_disabled();
     p->ring = std::min(nz, fp64 ? 4 : 8);
     p->thr_fwd_fused = std::max(p->thr_fwd_rows, p->thr_cols);
     p->smem_fwd_fused = std::max((size_t)npair * p->bs_row * csz, (size_t)tw * p->bs_col * csz);

@@ -38,6 +38,58 @@ template <typename R> ColsTmaFn pick_cols_tma(int n, bool inv);  // nullptr if n
         case 1024: return KERNEL<float, 1024 __VA_ARGS__>;             \
         default: return DEFAULT;                                       \
     }
+// Extended FP32 compile-time lengths: every other 2^a 3^b 5^c length from
+// 128 to 512 (the sizes a serving workload of such grids meets).  They get the
+// default kernels only, compiled in groups of up to 8 lengths, rows and
+// columns apart, so that the translation units build in parallel
+// (kern_f32_ext.cu, compiled once per group and part).
+#define MP_F32_CT_EXT1(F) F(135) F(144) F(150) F(160) F(162) F(180) F(200) F(216)
+#define MP_F32_CT_EXT2(F) F(225) F(240) F(243) F(250) F(270) F(288) F(300) F(320)
+#define MP_F32_CT_EXT3(F) F(324) F(360) F(375) F(384) F(400) F(405) F(432) F(450)
+#define MP_F32_CT_EXT4(F) F(480) F(486) F(500)
+// FP32 lengths that also have the opt-in variants (persistent, TMA, fused)
+#define MP_F32_CT_CORE(F) F(64) F(96) F(128) F(192) F(256) F(512) F(1024)
+
+namespace mp {
+enum KernelKind { kFwdRows = 0, kInvRows = 1, kFwdCols = 2, kInvCols = 3 };
+// group g (1..4), part 0 (rows: kFwdRows, kInvRows) or 1 (columns); nullptr
+// when n is not in the group or kind not in the part
+#define MP_EXT_DECL(G, P) KernelFn pick_f32_ext_##G##_##P(KernelKind kind, int n);
+MP_EXT_DECL(1, 0) MP_EXT_DECL(1, 1) MP_EXT_DECL(2, 0) MP_EXT_DECL(2, 1)
+MP_EXT_DECL(3, 0) MP_EXT_DECL(3, 1) MP_EXT_DECL(4, 0) MP_EXT_DECL(4, 1)
+#undef MP_EXT_DECL
+inline KernelFn pick_f32_ext(KernelKind kind, int n) {
+    KernelFn (*const fns[])(KernelKind, int) = {pick_f32_ext_1_0, pick_f32_ext_1_1, pick_f32_ext_2_0,
+                                                pick_f32_ext_2_1, pick_f32_ext_3_0, pick_f32_ext_3_1,
+                                                pick_f32_ext_4_0, pick_f32_ext_4_1};
+    for (auto f : fns)
+        if (KernelFn k = f(kind, n)) return k;
+    return nullptr;
+}
+// FP32 lengths with a compile-time plan (core or extended)
+inline bool ct_length_f32(int n) {
+#define MP_CT_CASE(N) case N:
+    switch (n) {
+        MP_F32_CT_CORE(MP_CT_CASE)
+        MP_F32_CT_EXT1(MP_CT_CASE) MP_F32_CT_EXT2(MP_CT_CASE) MP_F32_CT_EXT3(MP_CT_CASE) MP_F32_CT_EXT4(MP_CT_CASE)
+            return true;
+        default:
+            return false;
+    }
+#undef MP_CT_CASE
+}
+inline bool ct_core_f32(int n) {
+#define MP_CT_CASE(N) case N:
+    switch (n) {
+        MP_F32_CT_CORE(MP_CT_CASE)
+            return true;
+        default:
+            return false;
+    }
+#undef MP_CT_CASE
+}
+}  // namespace mp
+
 #define MP_PICK_F64(KERNEL, DEFAULT, ...)                              \
     switch (n) {                                                       \
         case 64: return KERNEL<double, 64 __VA_ARGS__>;                \

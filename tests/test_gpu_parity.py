@@ -81,7 +81,10 @@ def test_64cube_uniform(prec):
 @pytest.mark.parametrize("shape", [(48, 40, 12), (96, 96, 20), (30, 45, 7), (75, 64, 9),
                                    (15, 16, 5), (160, 20, 6), (2, 8, 3), (8, 2, 4),
                                    (128, 192, 8), (192, 128, 5), (512, 256, 3), (256, 512, 3),
-                                   (1024, 64, 3), (64, 1024, 2)])
+                                   (1024, 64, 3), (64, 1024, 2),
+                                   # extended compile-time lengths (FP32), odd and radix-3/5 ones
+                                   (135, 150, 4), (375, 243, 3), (500, 405, 2), (162, 486, 2),
+                                   (225, 288, 3), (480, 320, 2), (250, 243, 2)])
 def test_ragged_and_mixed_radix(shape, prec):
     nx, ny, nz = shape
     g = W.make_grid(nx, ny, nz, 25.0, 20.0, W.geometric_dz(nz, 10.0, 100.0))
