@@ -412,6 +412,53 @@ __device__ __forceinline__ void ct_last(const cplx<R>* buf, int nb, int bstride,
     }
 }
 
+// Last stage with a prefetch: pre(b, q, NS, i) runs for every butterfly i
+// of the thread before any butterfly is transformed, so loads it issues (the
+// operands of the store's read-modify-write) are all in flight at once
+// instead of one butterfly at a time; then store(b, q, x, NS, i) as ct_last.
+template <typename R, int N, int S, bool BFAST, class Pre, class Store>
+__device__ __forceinline__ void ct_last_pre(const cplx<R>* buf, int nb, int bstride, const cplx<R>* __restrict__ tws,
+                                            Pre&& pre, Store&& store) {
+    constexpr int NS = LastNs<R, N>::value;
+    const cplx<R>* __restrict__ tw = tws + StageIndex<R, N, NS>::value * N;
+    using SI = StageInfo<R, N, NS>;
+    static_assert(SI::LAST, "last stage");
+    constexpr int RAD = SI::RAD, NQ = SI::NQ;
+    constexpr int E = ElemsPerThread<R>::value;
+    constexpr int NB = (E + RAD - 1) / RAD;
+    const int total = NQ * nb;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int t = threadIdx.x + i * blockDim.x;
+        if (t < total) {
+            int b, q;
+            bfly_map<BFAST, NQ>(t, nb, b, q);
+            pre(b, q, NS, i);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int t = threadIdx.x + i * blockDim.x;
+        if (t < total) {
+            int b, q;
+            bfly_map<BFAST, NQ>(t, nb, b, q);
+            const cplx<R>* src = buf + b * bstride;
+            cplx<R> x[RAD];
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) x[r] = src[spad(q + r * NQ)];
+            if (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < RAD; ++r) {
+                    const cplx<R> wv = __ldg(&tw[r * NS + q]);
+                    x[r] = (S < 0) ? cmul(x[r], wv) : cmulc(x[r], wv);
+                }
+            }
+            RegFFT<R, RAD, S>::run(x);
+            store(b, q, x, NS, i);
+        }
+    }
+}
+
 // Last stage for an output buffer that aliases the input: every thread
 // computes its butterflies into registers, the block synchronises, then the
 // results go to store(b, q, x, NS).

@@ -416,8 +416,13 @@ __device__ __forceinline__ void tridiag_column_inplace(const ProjParams& p, size
 }
 
 // FP64 arithmetic on FP32 storage (near-zero wavenumbers of a mixed plan):
-// y.x in S[k] and y.y in G[k] (each slot reinterpreted as one double), 1/e in Gp.
+// y.x in S[k] and y.y in G[k] (each slot reinterpreted as one double), 1/e in
+// Gp.  Loads go out kTriBatch64 levels at a time before the levels' stores,
+// so a column waits on DRAM once per batch rather than once per level.
+constexpr int kTriBatch64 = 8;
+
 __device__ __forceinline__ void tridiag_column_mixed64(const ProjParams& p, size_t base, double lam, bool mean) {
+    constexpr int B = kTriBatch64;
     const int nz = p.nz;
     const size_t LS = (size_t)p.ny * p.nxp;
     float2* S = (float2*)p.S;
@@ -428,32 +433,52 @@ __device__ __forceinline__ void tridiag_column_mixed64(const ProjParams& p, size
     const double scale = p.scale;
     double g = 0.0;
     double2 y = make_double2(0.0, 0.0);
-    for (int k = 0; k < nz; ++k) {
-        const size_t o = k * LS + base;
-        const float2 dv = S[o];
-        const double ak = p.acoef[k];
-        const double m = ak * g;
-        const double e = lam * p.svol[k] - p.csum[k] - ak * m;
-        double gk = 1.0 / e;
-        double2 yk = make_double2((double)dv.x - m * y.x, (double)dv.y - m * y.y);
-        if (mean && k == 0) { gk = 0.0; yk = make_double2(0.0, 0.0); }
-        g = gk;
-        y = yk;
-        Sd[o] = yk.x;
-        Gd[o] = yk.y;
-        Gp[o] = gk;
+    for (int kb = 0; kb < nz; kb += B) {
+        float2 dv[B];
+#pragma unroll
+        for (int i = 0; i < B; ++i) dv[i] = (kb + i < nz) ? S[(kb + i) * LS + base] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            const int k = kb + i;
+            if (k >= nz) break;
+            const size_t o = k * LS + base;
+            const double ak = p.acoef[k];
+            const double m = ak * g;
+            const double e = lam * p.svol[k] - p.csum[k] - ak * m;
+            double gk = 1.0 / e;
+            double2 yk = make_double2((double)dv[i].x - m * y.x, (double)dv[i].y - m * y.y);
+            if (mean && k == 0) { gk = 0.0; yk = make_double2(0.0, 0.0); }
+            g = gk;
+            y = yk;
+            Sd[o] = yk.x;
+            Gd[o] = yk.y;
+            Gp[o] = gk;
+        }
     }
     double2 ph = make_double2(y.x * g, y.y * g);
     S[(nz - 1) * LS + base] = make_float2((float)(ph.x * scale), (float)(ph.y * scale));
-    for (int k = nz - 2; k >= 0; --k) {
-        const size_t o = k * LS + base;
-        const double yx = Sd[o], yy = Gd[o], gk = Gp[o];
-        const double a1 = p.acoef[k + 1];
-        const double2 pn = make_double2((yx - a1 * ph.x) * gk, (yy - a1 * ph.y) * gk);
-        const double iz = p.idzn[k + 1] * scale;
-        G[o + LS] = make_float2((float)((ph.x - pn.x) * iz), (float)((ph.y - pn.y) * iz));
-        S[o] = make_float2((float)(pn.x * scale), (float)(pn.y * scale));
-        ph = pn;
+    for (int kb = nz - 2; kb >= 0; kb -= B) {
+        double yx[B], yy[B], gv[B];
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            const int k = kb - i;
+            const size_t o = (k >= 0 ? k : 0) * LS + base;
+            yx[i] = (k >= 0) ? Sd[o] : 0.0;
+            yy[i] = (k >= 0) ? Gd[o] : 0.0;
+            gv[i] = (k >= 0) ? Gp[o] : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            const int k = kb - i;
+            if (k < 0) break;
+            const size_t o = k * LS + base;
+            const double a1 = p.acoef[k + 1];
+            const double2 pn = make_double2((yx[i] - a1 * ph.x) * gv[i], (yy[i] - a1 * ph.y) * gv[i]);
+            const double iz = p.idzn[k + 1] * scale;
+            G[o + LS] = make_float2((float)((ph.x - pn.x) * iz), (float)((ph.y - pn.y) * iz));
+            S[o] = make_float2((float)(pn.x * scale), (float)(pn.y * scale));
+            ph = pn;
+        }
     }
 }
 
@@ -545,8 +570,12 @@ __device__ __forceinline__ void tridiag_column_ckpt32(const ProjParams& p, size_
 // small |lambda| (the FP64 ones of a mixed plan, limited by the FP64 rate) sit at
 // both ends of the ky range and so start in the first wave of blocks, where
 // they overlap the FP32 columns instead of forming a tail.
+// One warp per block: the hardware deals blocks out to the SMs in turn, so
+// the FP64 warps (which share an SM's few FP64 units) land on distinct SMs.
+constexpr int kTriThreads = 32;
+
 template <typename R>
-__global__ void __launch_bounds__(128, 8) k_tridiag(ProjParams p) {
+__global__ void __launch_bounds__(kTriThreads, 1024 / kTriThreads) k_tridiag(ProjParams p) {
     const int nxw = (p.nxh + 31) & ~31;
     const long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int r = (int)(col / nxw);
@@ -752,26 +781,36 @@ __global__ void __launch_bounds__(512) k_inv_rows(ProjParams p) {
         };
         ct_first<R, NX, 1, false>(bufA, npr, bs, load);
         CtMid<R, NX, StageInfo<R, NX, 1>::NEXT, 1>::run(bufA, npr, bs, ctab<R>(p.twx));
-        auto store = [&](int b, int q, const C* x, int ns) {
-            constexpr int RAD = StageInfo<R, NX, LastNs<R, NX>::value>::RAD;
+        // the correction reads u, v or w where it writes them (outputs may
+        // alias inputs): every value this thread will update is loaded before
+        // the last stage writes any
+        constexpr int LRAD = StageInfo<R, NX, LastNs<R, NX>::value>::RAD;
+        constexpr int LNB = (ElemsPerThread<R>::value + LRAD - 1) / LRAD;
+        R prev[LNB][2][LRAD];
+        auto pre = [&](int b, int q, int ns, int i) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = j0 + 2 * b + h;
+                const size_t row = (size_t)k * plane + (size_t)j * NX + q;
+#pragma unroll
+                for (int r = 0; r < LRAD; ++r) prev[i][h][r] = (ch < 3 && j < ny) ? in[row + r * ns] : (R)0;
+            }
+        };
+        auto store = [&](int b, int q, const C* x, int ns, int i) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int j = j0 + 2 * b + h;
                 if (j >= ny) continue;
                 const size_t row = (size_t)k * plane + (size_t)j * NX + q;
-                // read every input first, then write (outputs may alias inputs)
-                R prev[RAD];
 #pragma unroll
-                for (int r = 0; r < RAD; ++r) prev[r] = (ch < 3) ? in[row + r * ns] : (R)0;
-#pragma unroll
-                for (int r = 0; r < RAD; ++r) {
+                for (int r = 0; r < LRAD; ++r) {
                     const R val = h ? x[r].y : x[r].x;
-                    out[row + r * ns] = (ch < 3) ? prev[r] - val : val;
+                    out[row + r * ns] = (ch < 3) ? prev[i][h][r] - val : val;
                     if (ch == 2 && k == nz - 1) out[row + r * ns + plane] = (R)0;
                 }
             }
         };
-        ct_last<R, NX, 1, false>(bufA, npr, bs, ctab<R>(p.twx), store);
+        ct_last_pre<R, NX, 1, false>(bufA, npr, bs, ctab<R>(p.twx), pre, store);
     } else {
         const int k = blockIdx.x / nrb;
         const int j0 = (blockIdx.x - k * nrb) * p.rows_inv;

@@ -368,7 +368,7 @@ int launch_solve(monc_proj_plan_s* p, const ProjParams& q, cudaStream_t st) {
         pick_fwd_fused<R>(p->nx)<<<p->grid_fwd_fused, p->thr_fwd_fused, p->smem_fwd_fused, st>>>(q);
         pm.end(5, st);
         pm.start(2, st);
-        pick_tridiag<R>()<<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(q);
+        pick_tridiag<R>()<<<(unsigned)((ncol + kTriThreads - 1) / kTriThreads), kTriThreads, 0, st>>>(q);
         pm.end(2, st);
         pm.start(6, st);
         pick_inv_fused<R>(p->nx)<<<p->grid_inv_fused, p->thr_inv_fused[inv_idx], p->smem_inv_fused[inv_idx], st>>>(q);
@@ -386,7 +386,7 @@ int launch_solve(monc_proj_plan_s* p, const ProjParams& q, cudaStream_t st) {
             ks.fwd_cols<<<n_fcols, p->thr_cols, p->smem_fcols, st>>>(q);
         pm.end(1, st);
         pm.start(2, st);
-        pick_tridiag<R>()<<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(q);
+        pick_tridiag<R>()<<<(unsigned)((ncol + kTriThreads - 1) / kTriThreads), kTriThreads, 0, st>>>(q);
         pm.end(2, st);
         pm.start(3, st);
         if (p->persist_cols && cudaMemsetAsync(q.sync, 0, sizeof(unsigned), st) != cudaSuccess) {
