@@ -570,9 +570,10 @@ __device__ __forceinline__ void tridiag_column_ckpt32(const ProjParams& p, size_
 // small |lambda| (the FP64 ones of a mixed plan, limited by the FP64 rate) sit at
 // both ends of the ky range and so start in the first wave of blocks, where
 // they overlap the FP32 columns instead of forming a tail.
-// One warp per block: the hardware deals blocks out to the SMs in turn, so
-// the FP64 warps (which share an SM's few FP64 units) land on distinct SMs.
-constexpr int kTriThreads = 32;
+// Threads per block of the vertical solve (one column each).  One-warp
+// blocks, which spread the FP64 warps over more SMs, measured no faster and
+// spill more registers.
+constexpr int kTriThreads = 128;
 
 template <typename R>
 __global__ void __launch_bounds__(kTriThreads, 1024 / kTriThreads) k_tridiag(ProjParams p) {
