@@ -209,22 +209,29 @@ constexpr int kMaxRadixF32 = 32;
 constexpr int kMaxRadixF64 = 16;
 template <typename R> struct ElemsPerThread { static constexpr int value = sizeof(R) == 4 ? kMaxRadixF32 : kMaxRadixF64; };
 
-// Radix of the next stage for the remaining length M (largest first).
+// Radix of the next compile-time stage for the remaining length M with E
+// elements per thread: the largest power of two from 8 to E that divides M;
+// else the largest divisor d <= E whose ceil(E/d) butterflies per thread
+// hold at most E + E/2 elements (so lengths with factors 3 and 5 take few,
+// composite-radix stages: 384 = 32*12, 500 = 20*5*5, 450 = 18*25 -> 18*5*5).
+// The host builds the twiddle tables of compile-time lengths with the same rule.
+MP_HD constexpr int ct_radix(int M, int E) {
+    for (int r = E; r >= 8; r /= 2)
+        if (M % r == 0) return r;
+    for (int d = E; d >= 2; --d)
+        if (M % d == 0 && ((E + d - 1) / d) * d <= E + E / 2) return d;
+    return M;
+}
+
 template <typename R, int M> struct NextRadix {
-    static constexpr int maxr = ElemsPerThread<R>::value;
-    static constexpr int value = (maxr >= 32 && M % 32 == 0) ? 32 : (M % 16 == 0) ? 16 : (M % 8 == 0) ? 8
-                               : (M % 4 == 0) ? 4 : (M % 2 == 0) ? 2 : (M % 5 == 0) ? 5 : 3;
+    static constexpr int value = ct_radix(M, ElemsPerThread<R>::value);
 };
 
 // Position of the stage with the given Ns in the compile-time plan.
 template <typename R, int N> constexpr int stage_index_impl(int target) {
     int ns = 1, s = 0;
     while (ns < target) {
-        const int m = N / ns;
-        const int maxr = ElemsPerThread<R>::value;
-        const int rad = (maxr >= 32 && m % 32 == 0) ? 32 : (m % 16 == 0) ? 16 : (m % 8 == 0) ? 8
-                      : (m % 4 == 0) ? 4 : (m % 2 == 0) ? 2 : (m % 5 == 0) ? 5 : 3;
-        ns *= rad;
+        ns *= ct_radix(N / ns, ElemsPerThread<R>::value);
         ++s;
     }
     return s;
@@ -310,10 +317,7 @@ template <typename R, int N, int NS> struct StageInfo {
 template <typename R, int N> constexpr int last_stage_ns_impl() {
     int ns = 1;
     while (ns < N) {
-        const int m = N / ns;
-        const int maxr = ElemsPerThread<R>::value;
-        const int rad = (maxr >= 32 && m % 32 == 0) ? 32 : (m % 16 == 0) ? 16 : (m % 8 == 0) ? 8
-                      : (m % 4 == 0) ? 4 : (m % 2 == 0) ? 2 : (m % 5 == 0) ? 5 : 3;
+        const int rad = ct_radix(N / ns, ElemsPerThread<R>::value);
         if (ns * rad == N) return ns;
         ns *= rad;
     }

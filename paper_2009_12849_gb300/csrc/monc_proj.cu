@@ -121,7 +121,10 @@ FastDiv make_fastdiv(unsigned d) {
 
 // Stockham radix plan, largest radices first (32 at most in FP32, 16 in FP64
 // where a 32-point register DFT would not fit the register file).
-FftFactors factorize(int n, int maxrad) {
+// ct: the stages of a compile-time plan (ct_radix, the rule the kernels
+// unroll); otherwise the run-time plan's radices 32/16/8/4/2 (up to maxrad),
+// then 5, then 3.
+FftFactors factorize(int n, int maxrad, bool ct) {
     FftFactors f{};
     f.n = n;
     int m = n, s = 0, ns = 1;
@@ -135,10 +138,14 @@ FftFactors factorize(int n, int maxrad) {
         ns *= r;
         m /= r;
     };
-    for (int r : {32, 16, 8, 4, 2})
-        while (r <= maxrad && m % r == 0) push(r);
-    while (m % 5 == 0) push(5);
-    while (m % 3 == 0) push(3);
+    if (ct) {
+        while (m > 1) push(ct_radix(m, maxrad));
+    } else {
+        for (int r : {32, 16, 8, 4, 2})
+            while (r <= maxrad && m % r == 0) push(r);
+        while (m % 5 == 0) push(5);
+        while (m % 3 == 0) push(3);
+    }
     f.nstages = s;
     return f;
 }
@@ -501,10 +508,11 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     p->nx = nx; p->ny = ny; p->nz = nz; p->dx = dx; p->dy = dy; p->precision = precision;
     p->nxh = nx / 2 + 1;
     p->nxp = (p->nxh + 3) & ~3;
-    p->fx = factorize(nx, precision == MONC_PROJ_FP64 ? kMaxRadixF64 : kMaxRadixF32);
-    p->fy = factorize(ny, precision == MONC_PROJ_FP64 ? kMaxRadixF64 : kMaxRadixF32);
-
     const bool fp64 = precision == MONC_PROJ_FP64;
+    const int maxrad = fp64 ? kMaxRadixF64 : kMaxRadixF32;
+    p->fx = factorize(nx, maxrad, ct_length(nx, fp64));
+    p->fy = factorize(ny, maxrad, ct_length(ny, fp64));
+
     const size_t csz = fp64 ? 16 : 8;
     {
         int dev = 0, nsm = 0;
