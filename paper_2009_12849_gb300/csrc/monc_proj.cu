@@ -139,7 +139,7 @@ FftFactors factorize(int n, int maxrad, bool ct) {
         m /= r;
     };
     if (ct) {
-        while (m > 1) push(ct_radix(m, maxrad));
+        while (m > 1) push(ct_stage_radix(n, ns, maxrad));
     } else {
         for (int r : {32, 16, 8, 4, 2})
             while (r <= maxrad && m % r == 0) push(r);
