@@ -47,7 +47,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batch measurement")
-    ap.add_argument("--serve-requests", type=int, default=2000,
+    ap.add_argument("--serve-requests", type=int, default=10000,
                     help="requests of the serving measurement (0 skips it; the full recipe is 10000)")
     return ap.parse_args()
 
