@@ -30,7 +30,17 @@
  * FP64.  MONC_PROJ_MIXED: every field is float; divergence, horizontal
  * transforms and the correction run in FP32, the vertical solve (a3) runs in
  * FP64 for the columns whose conditioning needs it (near-zero horizontal
- * wavenumbers) and in FP32 for the rest.
+ * wavenumbers) and in FP32 for the rest.  MONC_PROJ_REFINED: every field is
+ * double; the solve runs three passes, each a mixed-precision solve for a
+ * potential (the divergence of the pass's input formed in FP64, FP32
+ * transforms) followed by the subtraction of that potential's exact discrete
+ * gradient in FP64.  Each pass's divergence is the previous passes' error, so
+ * each pass shrinks it by the mixed solver's relative accuracy: one pass
+ * leaves ~1e-7, two ~1e-11, three FP64-level relative error (the environment
+ * variable MONC_PROJ_REFINE_PASSES, 1..4, read when a plan is made, sets the
+ * count).  The workspace also holds one FP64 field.  This is the
+ * single-precision solve with a double-precision restart that the paper
+ * proposes as further work (§5).
  *
  * Errors.  Every call returns a monc_proj_status.  Nothing aborts, traps or
  * throws across this boundary.  Problems found on the device (a bounded
@@ -65,7 +75,8 @@ typedef enum {
 
 typedef enum {
     MONC_PROJ_FP64 = 0,
-    MONC_PROJ_MIXED = 1
+    MONC_PROJ_MIXED = 1,
+    MONC_PROJ_REFINED = 2
 } monc_proj_precision;
 
 /* Largest nx or ny a plan accepts. */
@@ -83,7 +94,7 @@ typedef enum {
  *   dz         host array [nz], layer thicknesses [m], > 0
  *   rho_c      host array [nz], reference density at cell centres, > 0
  *   rho_f      host array [nz+1], reference density at w faces, > 0
- *   precision  MONC_PROJ_FP64 or MONC_PROJ_MIXED
+ *   precision  MONC_PROJ_FP64, MONC_PROJ_MIXED or MONC_PROJ_REFINED
  *   stream     cudaStream_t (may be NULL) used for the plan's uploads; the
  *              call returns after they have completed
  *

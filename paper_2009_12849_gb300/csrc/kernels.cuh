@@ -49,6 +49,9 @@ struct ProjParams {
     int rows_inv;               // real rows per inverse row task (even)
     int nrb_inv;
     int nch;                    // real channels per row in the inverse (3, or 4 with phi)
+    int phi_only;               // 1: the inverse produces phi alone (refinement passes)
+    void* phi_pass;             // refinement passes: this pass's potential (FP64, [nz][ny][nx])
+    double* phi_mean;           // refinement passes: level-0 horizontal mean of the summed potential
     int tw_cols;                // kx columns per column task
     int ntiles;                 // column tasks per level
     int bs_row;                 // smem stride of a row transform (complex elements)
@@ -89,8 +92,10 @@ __device__ __forceinline__ cplx<R>* run_fft(cplx<R>* buf, int nb, int bs, const 
 // transform X_j[k] = (Z[k] + conj Z[n-k])/2, X_{j+1}[k] = (Z[k] - conj Z[n-k])/(2i).
 // Output is the level's x-spectrum in T, scaled by rho_c dz (the symmetric
 // form of the vertical operator).
+// F is the field type: R, or double with R = float for the refinement passes
+// (the divergence is formed in F, then rounded to the transform precision).
 // ---------------------------------------------------------------------------
-template <typename R, int NX>
+template <typename R, int NX, typename F = R>
 __global__ void __launch_bounds__(512) k_fwd_rows(ProjParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using C = cplx<R>;
@@ -102,17 +107,17 @@ __global__ void __launch_bounds__(512) k_fwd_rows(ProjParams p) {
     const int bs = p.bs_row;
     C* bufA = (C*)smem_raw;
 
-    const R* u = (const R*)p.u;
-    const R* v = (const R*)p.v;
-    const R* w = (const R*)p.w;
+    const F* u = (const F*)p.u;
+    const F* v = (const F*)p.v;
+    const F* w = (const F*)p.w;
     const size_t plane = (size_t)ny * nx;
-    const R sv = (R)p.svol[k];
-    const R rlo = (R)p.rflo[k];
-    const R rhi = (R)p.rfhi[k];
-    const R idx = (R)p.idx, idy = (R)p.idy;
+    const F sv = (F)p.svol[k];
+    const F rlo = (F)p.rflo[k];
+    const F rhi = (F)p.rfhi[k];
+    const F idx = (F)p.idx, idy = (F)p.idy;
 
     const C* res;
-    if constexpr (NX > 0 && NX % 4 == 0 && sizeof(R) == 4) {
+    if constexpr (NX > 0 && NX % 4 == 0 && sizeof(R) == 4 && sizeof(F) == 4) {
         // FP32, compile-time length: every thread takes groups of 4 adjacent
         // cells of a row and loads them as float4 (u, v, v of the row below,
         // w below and above), 4 groups in flight per thread.
@@ -173,11 +178,11 @@ __global__ void __launch_bounds__(512) k_fwd_rows(ProjParams p) {
         const int tot = p.rows_fwd * nx;
         const int step = kLoadBatch * blockDim.x;
         for (int base = threadIdx.x; base < tot; base += step) {
-            R uc[kLoadBatch], um[kLoadBatch], vc[kLoadBatch], vm[kLoadBatch], wl[kLoadBatch], wh[kLoadBatch];
+            F uc[kLoadBatch], um[kLoadBatch], vc[kLoadBatch], vm[kLoadBatch], wl[kLoadBatch], wh[kLoadBatch];
 #pragma unroll
             for (int c = 0; c < kLoadBatch; ++c) {
                 const int t = base + c * blockDim.x;
-                uc[c] = um[c] = vc[c] = vm[c] = wl[c] = wh[c] = (R)0;
+                uc[c] = um[c] = vc[c] = vm[c] = wl[c] = wh[c] = (F)0;
                 if (t < tot) {
                     const int r = (NX > 0) ? t / NX : t / nx;
                     const int i = t - r * nx;
@@ -201,10 +206,10 @@ __global__ void __launch_bounds__(512) k_fwd_rows(ProjParams p) {
                 if (t < tot) {
                     const int r = (NX > 0) ? t / NX : t / nx;
                     const int i = t - r * nx;
-                    const R hdiv = (uc[c] - um[c]) * idx + (vc[c] - vm[c]) * idy;
-                    const R d = sv * hdiv + (rhi * wh[c] - rlo * wl[c]);
+                    const F hdiv = (uc[c] - um[c]) * idx + (vc[c] - vm[c]) * idy;
+                    const F d = sv * hdiv + (rhi * wh[c] - rlo * wl[c]);
                     R* slot = (R*)&bufA[(r >> 1) * bs + spad(i)];
-                    slot[r & 1] = d;
+                    slot[r & 1] = (R)d;
                 }
             }
         }
@@ -656,7 +661,9 @@ __device__ __forceinline__ void inv_cols_ct_task(const ProjParams& p, int k, int
     ct_last<R, NY, 1, true>(buf, p.tw_cols, p.bs_col, ctab<R>(p.twy), store);
 }
 
-template <typename R, int NY>
+// PHI: the potential alone (refinement passes): kind 0 transforms the p^ tile
+// into Tphi, kind 1 does nothing.
+template <typename R, int NY, bool PHI = false>
 __global__ void __launch_bounds__(512) k_inv_cols(ProjParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using C = cplx<R>;
@@ -666,7 +673,9 @@ __global__ void __launch_bounds__(512) k_inv_cols(ProjParams p) {
         const int k = task / p.ntiles;
         const int kx0 = (task - k * p.ntiles) * p.tw_cols;
         C* buf = (C*)smem_raw;
-        if (kind == 0) {
+        if constexpr (PHI) {
+            if (kind == 0) inv_cols_ct_task<R, NY>(p, k, kx0, 3, buf);
+        } else if (kind == 0) {
             inv_cols_ct_task<R, NY>(p, k, kx0, 0, buf);
             __syncthreads();
             inv_cols_ct_task<R, NY>(p, k, kx0, 1, buf);
@@ -680,7 +689,7 @@ __global__ void __launch_bounds__(512) k_inv_cols(ProjParams p) {
         return;
     }
     const int nf = p.nch;
-    const int f = blockIdx.x % nf;
+    const int f = PHI ? 3 : blockIdx.x % nf;
     const int task = blockIdx.x / nf;
     const int k = task / p.ntiles;
     const int kx0 = (task - k * p.ntiles) * p.tw_cols;
@@ -740,8 +749,10 @@ __device__ __forceinline__ cplx<R> inv_spectrum(const ProjParams& p, int k, int 
 }
 
 // Compile-time lengths: one channel per task, task = (level, row block, channel).
-// Generic lengths: all channels of a row block in one task.
-template <typename R, int NX>
+// Generic lengths: all channels of a row block in one task.  F is the field
+// type (R, or double with R = float for the refinement passes: the gradient
+// is subtracted from the FP64 field in FP64).
+template <typename R, int NX, typename F = R>
 __global__ void __launch_bounds__(512) k_inv_rows(ProjParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using C = cplx<R>;
@@ -753,24 +764,25 @@ __global__ void __launch_bounds__(512) k_inv_rows(ProjParams p) {
     const size_t plane = (size_t)ny * nx;
     if constexpr (NX > 0) {
         constexpr int NXH = NX / 2 + 1;
-        const int ch = blockIdx.x % nch;
+        const int ch = p.phi_only ? 3 : blockIdx.x % nch;
         const int t2 = blockIdx.x / nch;
         const int k = t2 / nrb;
         const int j0 = (t2 - k * nrb) * p.rows_inv;
         const int npr = p.rows_inv / 2;              // transforms (row pairs) per task
-        R* out = (ch == 0) ? (R*)p.uo : (ch == 1) ? (R*)p.vo : (ch == 2) ? (R*)p.wo : (R*)p.phi;
+        F* out = (ch == 0) ? (F*)p.uo : (ch == 1) ? (F*)p.vo : (ch == 2) ? (F*)p.wo : (F*)p.phi;
         if (ch == 2 && k == 0) {
             // bottom face: w = 0
             for (int t = threadIdx.x; t < p.rows_inv * NX; t += blockDim.x) {
                 const int j = j0 + t / NX;
                 if (j < ny) {
-                    out[(size_t)j * NX + (t % NX)] = (R)0;
-                    if (nz == 1) out[plane + (size_t)j * NX + (t % NX)] = (R)0;   // top face too
+                    out[(size_t)j * NX + (t % NX)] = (F)0;
+                    if (nz == 1) out[plane + (size_t)j * NX + (t % NX)] = (F)0;   // top face too
                 }
             }
             return;
         }
-        const R* in = (ch == 0) ? (const R*)p.u : (ch == 1) ? (const R*)p.v : (const R*)p.w;
+        const F* in = (ch == 0) ? (const F*)p.u : (ch == 1) ? (const F*)p.v : (const F*)p.w;
+        const bool upd = ch < 3;
         const C* spec = inv_channel_spectrum<R>(p, ch) + (size_t)k * ny * p.nxp;
         const int nxp = p.nxp;
         auto load = [&](int b, int kx) -> C {
@@ -783,47 +795,71 @@ __global__ void __launch_bounds__(512) k_inv_rows(ProjParams p) {
         ct_first<R, NX, 1, false>(bufA, npr, bs, load);
         CtMid<R, NX, StageInfo<R, NX, 1>::NEXT, 1>::run(bufA, npr, bs, ctab<R>(p.twx));
         // the correction reads u, v or w where it writes them (outputs may
-        // alias inputs): every value this thread will update is loaded before
-        // the last stage writes any
+        // alias inputs)
         constexpr int LRAD = StageInfo<R, NX, LastNs<R, NX>::value>::RAD;
-        constexpr int LNB = (ElemsPerThread<R>::value + LRAD - 1) / LRAD;
-        R prev[LNB][2][LRAD];
-        auto pre = [&](int b, int q, int ns, int i) {
+        if constexpr (sizeof(F) == sizeof(R)) {
+            // every value this thread will update is loaded before the last
+            // stage writes any
+            constexpr int LNB = (ElemsPerThread<R>::value + LRAD - 1) / LRAD;
+            F prev[LNB][2][LRAD];
+            auto pre = [&](int b, int q, int ns, int i) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int j = j0 + 2 * b + h;
-                const size_t row = (size_t)k * plane + (size_t)j * NX + q;
+                for (int h = 0; h < 2; ++h) {
+                    const int j = j0 + 2 * b + h;
+                    const size_t row = (size_t)k * plane + (size_t)j * NX + q;
 #pragma unroll
-                for (int r = 0; r < LRAD; ++r) prev[i][h][r] = (ch < 3 && j < ny) ? in[row + r * ns] : (R)0;
-            }
-        };
-        auto store = [&](int b, int q, const C* x, int ns, int i) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int j = j0 + 2 * b + h;
-                if (j >= ny) continue;
-                const size_t row = (size_t)k * plane + (size_t)j * NX + q;
-#pragma unroll
-                for (int r = 0; r < LRAD; ++r) {
-                    const R val = h ? x[r].y : x[r].x;
-                    out[row + r * ns] = (ch < 3) ? prev[i][h][r] - val : val;
-                    if (ch == 2 && k == nz - 1) out[row + r * ns + plane] = (R)0;
+                    for (int r = 0; r < LRAD; ++r) prev[i][h][r] = (upd && j < ny) ? in[row + r * ns] : (F)0;
                 }
-            }
-        };
-        ct_last_pre<R, NX, 1, false>(bufA, npr, bs, ctab<R>(p.twx), pre, store);
+            };
+            auto store = [&](int b, int q, const C* x, int ns, int i) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int j = j0 + 2 * b + h;
+                    if (j >= ny) continue;
+                    const size_t row = (size_t)k * plane + (size_t)j * NX + q;
+#pragma unroll
+                    for (int r = 0; r < LRAD; ++r) {
+                        const F val = (F)(h ? x[r].y : x[r].x);
+                        out[row + r * ns] = (ch < 3) ? prev[i][h][r] - val : (upd ? prev[i][h][r] + val : val);
+                        if (ch == 2 && k == nz - 1) out[row + r * ns + plane] = (F)0;
+                    }
+                }
+            };
+            ct_last_pre<R, NX, 1, false>(bufA, npr, bs, ctab<R>(p.twx), pre, store);
+        } else {
+            // wider fields (refinement passes): one butterfly's operands at a
+            // time, which keeps the FP64 values in registers
+            auto store = [&](int b, int q, const C* x, int ns) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int j = j0 + 2 * b + h;
+                    if (j >= ny) continue;
+                    const size_t row = (size_t)k * plane + (size_t)j * NX + q;
+                    F prev[LRAD];
+#pragma unroll
+                    for (int r = 0; r < LRAD; ++r) prev[r] = upd ? in[row + r * ns] : (F)0;
+#pragma unroll
+                    for (int r = 0; r < LRAD; ++r) {
+                        const F val = (F)(h ? x[r].y : x[r].x);
+                        out[row + r * ns] = (ch < 3) ? prev[r] - val : (upd ? prev[r] + val : val);
+                        if (ch == 2 && k == nz - 1) out[row + r * ns + plane] = (F)0;
+                    }
+                }
+            };
+            ct_last<R, NX, 1, false>(bufA, npr, bs, ctab<R>(p.twx), store);
+        }
     } else {
         const int k = blockIdx.x / nrb;
         const int j0 = (blockIdx.x - k * nrb) * p.rows_inv;
         const int npr = p.rows_inv / 2;
         const int np = nch * npr;
-        const R* u = (const R*)p.u;
-        const R* v = (const R*)p.v;
-        const R* w = (const R*)p.w;
-        R* uo = (R*)p.uo;
-        R* vo = (R*)p.vo;
-        R* wo = (R*)p.wo;
-        R* ph = (R*)p.phi;
+        const F* u = (const F*)p.u;
+        const F* v = (const F*)p.v;
+        const F* w = (const F*)p.w;
+        F* uo = (F*)p.uo;
+        F* vo = (F*)p.vo;
+        F* wo = (F*)p.wo;
+        F* ph = (F*)p.phi;
         const int tot = np * nx;
         const int step = kLoadBatch * blockDim.x;
         for (int base = threadIdx.x; base < tot; base += step) {
@@ -838,8 +874,9 @@ __global__ void __launch_bounds__(512) k_inv_rows(ProjParams p) {
                     const int ch = q / npr;
                     const int m = q - ch * npr;
                     const int j = j0 + 2 * m;
-                    av[c] = inv_spectrum<R>(p, k, j, ch, kx);
-                    bv[c] = inv_spectrum<R>(p, k, j + 1, ch, kx);
+                    const int chs = p.phi_only ? 3 : ch;
+                    av[c] = inv_spectrum<R>(p, k, j, chs, kx);
+                    bv[c] = inv_spectrum<R>(p, k, j + 1, chs, kx);
                 }
             }
 #pragma unroll
@@ -857,16 +894,16 @@ __global__ void __launch_bounds__(512) k_inv_rows(ProjParams p) {
         const int tot2 = p.rows_inv * nx;
         const int step2 = kLoadBatch * blockDim.x;
         for (int base = threadIdx.x; base < tot2; base += step2) {
-            R uu[kLoadBatch], vv[kLoadBatch], ww[kLoadBatch];
+            F uu[kLoadBatch], vv[kLoadBatch], ww[kLoadBatch];
 #pragma unroll
             for (int c = 0; c < kLoadBatch; ++c) {
                 const int t = base + c * blockDim.x;
-                uu[c] = vv[c] = ww[c] = (R)0;
+                uu[c] = vv[c] = ww[c] = (F)0;
                 if (t < tot2) {
                     const int r = t / nx;
                     const int i = t - r * nx;
                     const int j = j0 + r;
-                    if (j < ny) {
+                    if (j < ny && !p.phi_only) {
                         const size_t o = (size_t)k * plane + (size_t)j * nx + i;
                         uu[c] = u[o];
                         vv[c] = v[o];
@@ -883,22 +920,89 @@ __global__ void __launch_bounds__(512) k_inv_rows(ProjParams p) {
                 const int j = j0 + r;
                 if (j >= ny) continue;
                 const int m = r >> 1;
-                R val[4];
+                F val[4] = {(F)0, (F)0, (F)0, (F)0};
 #pragma unroll
                 for (int ch = 0; ch < 4; ++ch) {
                     if (ch < nch) {
                         const C z = res[(ch * npr + m) * bs + spad(i)];
-                        val[ch] = (r & 1) ? z.y : z.x;
+                        val[ch] = (F)((r & 1) ? z.y : z.x);
                     }
                 }
                 const size_t o = (size_t)k * plane + (size_t)j * nx + i;
+                if (p.phi_only) {
+                    ph[o] = val[0];
+                    continue;
+                }
                 uo[o] = uu[c] - val[0];
                 vo[o] = vv[c] - val[1];
-                wo[o] = (k == 0) ? (R)0 : (R)(ww[c] - val[2]);
-                if (k == nz - 1) wo[o + plane] = (R)0;
+                wo[o] = (k == 0) ? (F)0 : (F)(ww[c] - val[2]);
+                if (k == nz - 1) wo[o + plane] = (F)0;
                 if (nch == 4) ph[o] = val[3];
             }
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Refinement passes, a5 in physical space: u -= (phi[i+1]-phi[i])/dx,
+// v -= (phi[j+1]-phi[j])/dy, w[k] -= (phi[k]-phi[k-1])/dzn[k] (w = 0 on the
+// bottom and top faces), all in F, with phi this pass's potential (periodic
+// in x and y).  The correction is then the exact discrete gradient of a
+// stored potential, so the next pass's divergence is exactly this pass's
+// remaining error.  phi_sum (optional) accumulates the passes' potentials;
+// on the last pass it also subtracts *mean_sub, the level-0 horizontal mean of
+// the sum (the pin of the potential: the FP32 transforms leave each pass's
+// potential a rounding-size constant off, which no later pass can see).
+// One block row per (level, row).
+// ---------------------------------------------------------------------------
+template <typename F>
+__global__ void __launch_bounds__(256) k_fd_correct(ProjParams p, const F* __restrict__ phi, F* phi_sum,
+                                                    int accumulate, const double* mean_sub) {
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int k = blockIdx.x / ny;
+    const int j = blockIdx.x - k * ny;
+    const size_t plane = (size_t)ny * nx;
+    const size_t row = (size_t)k * plane + (size_t)j * nx;
+    const size_t rowp = (size_t)k * plane + (size_t)(j + 1 == ny ? 0 : j + 1) * nx;
+    const F* u = (const F*)p.u;
+    const F* v = (const F*)p.v;
+    const F* w = (const F*)p.w;
+    F* uo = (F*)p.uo;
+    F* vo = (F*)p.vo;
+    F* wo = (F*)p.wo;
+    const F idx = (F)p.idx, idy = (F)p.idy;
+    const F iz = (F)p.idzn[k];
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const F ph = phi[row + i];
+        const F pe = phi[row + (i + 1 == nx ? 0 : i + 1)];
+        const F pn = phi[rowp + i];
+        const F uu = u[row + i], vv = v[row + i];
+        const F ww = (k > 0) ? w[row + i] : (F)0;
+        const F pb = (k > 0) ? phi[row - plane + i] : (F)0;
+        uo[row + i] = uu - (pe - ph) * idx;
+        vo[row + i] = vv - (pn - ph) * idy;
+        wo[row + i] = (k > 0) ? ww - (ph - pb) * iz : (F)0;
+        if (k == nz - 1) wo[row + plane + i] = (F)0;
+        if (phi_sum) {
+            const F sum = accumulate ? phi_sum[row + i] + ph : ph;
+            phi_sum[row + i] = mean_sub ? sum - (F)*mean_sub : sum;
+        }
+    }
+}
+
+// *acc += mean of phi[0..n) (one block; FP64 sums).
+template <typename F>
+__global__ void __launch_bounds__(1024) k_mean_add(const F* __restrict__ phi, int n, double* acc) {
+    __shared__ double part[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)phi[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < (blockDim.x + 31) / 32) ? part[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) *acc += s / (double)n;
     }
 }
 

@@ -44,6 +44,7 @@ struct monc_proj_plan_s {
     bool ct_rows;                         // compile-time length along x
     bool ct_cols;                         // compile-time length along y
     bool fused;                           // square compile-time grid: fused persistent kernels
+    int refine_passes;                    // MONC_PROJ_REFINED: passes per solve
     bool tma_cols;                        // FP32 compile-time column lengths: TMA-staged column kernels
     size_t smem_tma;                      // their dynamic shared memory (two tile buffers)
     int ring;                             // levels in the L2 rings of the fused kernels
@@ -56,7 +57,7 @@ struct monc_proj_plan_s {
     size_t smem_fwd_rows, smem_cols, smem_fcols, smem_inv_rows[2];
     // workspace layout
     size_t ws_bytes;
-    size_t off_S, off_G, off_T, off_Tp, off_Tgy, off_Tgz, off_Tphi, off_Y, off_Gp;
+    size_t off_S, off_G, off_T, off_Tp, off_Tgy, off_Tgz, off_Tphi, off_Y, off_Gp, off_phipass, off_phimean;
     // per-phase timing
     bool profiling;
     int nprof;
@@ -261,6 +262,8 @@ ProjParams make_params(const monc_proj_plan_s* p, const void* u, const void* v, 
     q.Tp = b + p->off_Tp; q.Tgy = b + p->off_Tgy; q.Tgz = b + p->off_Tgz; q.Tphi = b + p->off_Tphi;
     q.Y = (double2*)(b + p->off_Y); q.Gp = (double*)(b + p->off_Gp);
     q.sync = (unsigned*)(b + p->off_sync);
+    q.phi_pass = b + p->off_phipass;
+    q.phi_mean = (double*)(b + p->off_phimean);
     q.ring = p->fused ? p->ring : nz_all_levels(p);
     q.lag = p->lag;
     q.err = p->err;
@@ -292,10 +295,12 @@ struct SolveKernels {
 
 template <typename R> SolveKernels pick_kernels(const monc_proj_plan_s* p) {
     const int nx = p->nx, ny = p->ny;
-    return SolveKernels{pick_k_fwd_rows<R>(nx),
+    const bool ref = p->precision == MONC_PROJ_REFINED;
+    return SolveKernels{ref ? pick_refined_fwd_rows(nx) : pick_k_fwd_rows<R>(nx),
                         pick_k_fwd_cols<R>(ny),
-                        p->persist_cols ? pick_inv_cols_persist<R>(ny) : pick_k_inv_cols<R>(ny),
-                        pick_k_inv_rows<R>(nx)};
+                        ref ? pick_refined_inv_cols(ny)
+                            : p->persist_cols ? pick_inv_cols_persist<R>(ny) : pick_k_inv_cols<R>(ny),
+                        ref ? pick_refined_inv_rows(nx) : pick_k_inv_rows<R>(nx)};
 }
 
 // ---------------------------------------------------------------------------
@@ -411,6 +416,50 @@ int launch_solve(monc_proj_plan_s* p, const ProjParams& q, cudaStream_t st) {
     return e == cudaSuccess ? MONC_PROJ_OK : MONC_PROJ_ECUDA;
 }
 
+// One projection on a plan.  Refinement plans run kRefinePasses passes on the
+// FP64 fields: each pass solves for a potential with the mixed pipeline (the
+// divergence of the pass's input formed in FP64) and subtracts that
+// potential's discrete gradient in FP64.  The correction is an exact gradient,
+// so the next pass's divergence is exactly the remaining error, and each pass
+// shrinks it by the mixed solver's relative accuracy; phi is the sum of the
+// passes' potentials.
+constexpr int kRefinePasses = 3;                  // default; MONC_PROJ_REFINE_PASSES overrides (1..4)
+
+int run_solve(monc_proj_plan_s* p, const ProjParams& q, cudaStream_t st) {
+    if (p->precision == MONC_PROJ_FP64) return launch_solve<double>(p, q, st);
+    if (p->precision != MONC_PROJ_REFINED) return launch_solve<float>(p, q, st);
+    const int npass = p->refine_passes;
+    for (int pass = 0; pass < npass; ++pass) {
+        // the mixed pipeline produces this pass's potential alone ...
+        ProjParams qp = q;
+        if (pass > 0) {
+            qp.u = q.uo;
+            qp.v = q.vo;
+            qp.w = q.wo;
+        }
+        qp.phi = q.phi_pass;
+        qp.phi_only = 1;
+        qp.nch = 1;
+        qp.rows_inv = p->rows_inv[0];
+        qp.nrb_inv = (p->ny + qp.rows_inv - 1) / qp.rows_inv;
+        const int rc = launch_solve<float>(p, qp, st);
+        if (rc != MONC_PROJ_OK) return rc;
+        // ... and the correction subtracts its exact discrete gradient in FP64
+        const bool last = pass + 1 == npass;
+        if (q.phi) {
+            if (pass == 0 && cudaMemsetAsync(q.phi_mean, 0, sizeof(double), st) != cudaSuccess) {
+                cudaGetLastError();
+                return MONC_PROJ_ECUDA;
+            }
+            k_mean_add<double><<<1, 1024, 0, st>>>((const double*)q.phi_pass, p->nx * p->ny, q.phi_mean);
+        }
+        k_fd_correct<double><<<p->nz * p->ny, 256, 0, st>>>(qp, (const double*)q.phi_pass, (double*)q.phi,
+                                                            pass > 0 ? 1 : 0, last ? q.phi_mean : nullptr);
+        if (cudaGetLastError() != cudaSuccess) return MONC_PROJ_ECUDA;
+    }
+    return MONC_PROJ_OK;
+}
+
 // Raise the dynamic shared-memory limit of the kernels a plan uses; fails if
 // the plan's blocks need more than the device allows.  The L1/shared carveout
 // is left to the driver: forcing the largest shared carveout (least L1)
@@ -483,7 +532,8 @@ int plan_kernel_attrs(monc_proj_plan_s* p) {
 int validate_grid(int nx, int ny, int nz, double dx, double dy, const double* dz,
                   const double* rho_c, const double* rho_f, int precision) {
     if (nx < 1 || ny < 1 || nz < 1 || !dz || !rho_c || !rho_f) return MONC_PROJ_EINVAL;
-    if (precision != MONC_PROJ_FP64 && precision != MONC_PROJ_MIXED) return MONC_PROJ_EINVAL;
+    if (precision != MONC_PROJ_FP64 && precision != MONC_PROJ_MIXED && precision != MONC_PROJ_REFINED)
+        return MONC_PROJ_EINVAL;
     if (!finite_pos(dx) || !finite_pos(dy)) return MONC_PROJ_EINVAL;
     for (int k = 0; k < nz; ++k)
         if (!finite_pos(dz[k]) || !finite_pos(rho_c[k])) return MONC_PROJ_EINVAL;
@@ -510,8 +560,12 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     p->nxp = (p->nxh + 3) & ~3;
     const bool fp64 = precision == MONC_PROJ_FP64;
     const int maxrad = fp64 ? kMaxRadixF64 : kMaxRadixF32;
-    p->fx = factorize(nx, maxrad, ct_length(nx, fp64));
-    p->fy = factorize(ny, maxrad, ct_length(ny, fp64));
+    // compile-time plans along x and y (refinement passes: the x kernels on
+    // FP64 fields exist for the core lengths only)
+    const bool ctx = ct_length(nx, fp64) && (precision != MONC_PROJ_REFINED || ct_core_length(nx, false));
+    const bool cty = ct_length(ny, fp64) && (precision != MONC_PROJ_REFINED || ct_core_length(ny, false));
+    p->fx = factorize(nx, maxrad, ctx);
+    p->fy = factorize(ny, maxrad, cty);
 
     const size_t csz = fp64 ? 16 : 8;
     {
@@ -612,7 +666,6 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     // elements (E = the largest radix: 32 FP32, 16 FP64).  Run-time lengths:
     // two buffers (ping-pong) within ~96 KB, 256 threads.
     const int E = fp64 ? kMaxRadixF64 : kMaxRadixF32;
-    const bool ctx = ct_length(nx, fp64), cty = ct_length(ny, fp64);
     p->bs_row = spad_len(nx);
     // column tiles: a pitch of 4 (mod 16) complex elements spreads the
     // columns of a tile over distinct shared-memory banks
@@ -636,11 +689,11 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     p->smem_fcols = p->smem_cols;
     // the persistent inverse column kernel (opt-in) holds two input stages
     // of ny x tw values plus the FFT buffer
-    p->persist_cols = cty && ct_core_length(ny, fp64) && persist_cols_enabled();
+    p->persist_cols = cty && ct_core_length(ny, fp64) && precision != MONC_PROJ_REFINED && persist_cols_enabled();
     // TMA column kernels (opt-in): FP32 compile-time lengths (rows of tw >= 2
     // complex values, a multiple of 16 bytes)
     p->smem_tma = (size_t)2 * tw * p->bs_col * csz + 128 + 32;    // + alignment slack, mbarriers
-    p->tma_cols = !fp64 && cty && ct_core_length(ny, fp64) && !p->persist_cols && (tw * csz) % 16 == 0 && p->smem_tma <= kSmemMax &&
+    p->tma_cols = !fp64 && cty && ct_core_length(ny, fp64) && precision != MONC_PROJ_REFINED && !p->persist_cols && (tw * csz) % 16 == 0 && p->smem_tma <= kSmemMax &&
                   tma_enabled() && tmap_encoder() != nullptr;
     if (p->persist_cols) p->smem_cols = ((size_t)2 * ny * tw + (size_t)tw * p->bs_col) * csz;
     p->ct_rows = ctx;
@@ -666,7 +719,8 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
 
     // fused persistent kernels for square compile-time grids: one block size
     // and shared-memory size for both task kinds of each kernel
-    p->fused = ctx && cty && nx == ny && ct_core_length(nx, fp64) && !fused_disabled();
+    p->fused = ctx && cty && nx == ny && ct_core_length(nx, fp64) && precision != MONC_PROJ_REFINED &&
+               !fused_disabled();
     p->ring = std::min(nz, fp64 ? 4 : 8);
     p->thr_fwd_fused = std::max(p->thr_fwd_rows, p->thr_cols);
     p->smem_fwd_fused = std::max((size_t)npair * p->bs_row * csz, (size_t)tw * p->bs_col * csz);
@@ -695,6 +749,11 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     p->off_sync = off;                                // tickets and per-level counters of the fused kernels
     p->sync_bytes = (size_t)(2 + 10 * nz) * sizeof(unsigned);
     off = align256(off + p->sync_bytes);
+    p->refine_passes = std::min(4, env_int("MONC_PROJ_REFINE_PASSES", kRefinePasses));
+    p->off_phipass = off;                             // refinement passes: one pass's potential (FP64)
+    if (precision == MONC_PROJ_REFINED) off = align256(off + (size_t)nx * ny * nz * sizeof(double));
+    p->off_phimean = off;                             // refinement passes: level-0 mean of the potential
+    if (precision == MONC_PROJ_REFINED) off = align256(off + sizeof(double));
     p->ws_bytes = off;
 }
 
@@ -807,8 +866,7 @@ int monc_proj_solve(monc_proj_plan_t plan, const void* u, const void* v, const v
     if (((uintptr_t)workspace) & 255) return MONC_PROJ_EINVAL;
     ProjParams q = make_params(plan, u, v, w, u_out, v_out, w_out, phi_out, workspace);
     cudaStream_t st = (cudaStream_t)stream;
-    if (plan->precision == MONC_PROJ_FP64) return launch_solve<double>(plan, q, st);
-    return launch_solve<float>(plan, q, st);
+    return run_solve(plan, q, st);
 }
 
 int monc_proj_batch_workspace_size(const monc_proj_plan_t* plans, int count, size_t* bytes) {
@@ -1016,6 +1074,5 @@ extern "C" int monc_proj_solve_noalloc(int nx, int ny, int nz, double dx, double
     unsigned char* b = (unsigned char*)base;
     plan_bind(&plan, b, to);
     const ProjParams q = make_params(&plan, u, v, w, u_out, v_out, w_out, phi_out, b + tables);
-    if (plan.precision == MONC_PROJ_FP64) return launch_solve<double>(&plan, q, st);
-    return launch_solve<float>(&plan, q, st);
+    return run_solve(&plan, q, st);
 }

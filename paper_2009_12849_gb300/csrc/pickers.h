@@ -22,6 +22,10 @@ template <typename R> KernelFn pick_inv_cols_persist(int n);
 template <typename R> KernelFn pick_fwd_fused(int n);
 template <typename R> KernelFn pick_inv_fused(int n);
 template <typename R> KernelFn pick_tridiag();
+// refinement passes: FP32 transforms on FP64 fields (row kernels with F = double)
+KernelFn pick_refined_fwd_rows(int n);
+KernelFn pick_refined_inv_rows(int n);
+KernelFn pick_refined_inv_cols(int n);   // the potential alone
 template <typename R> ColsTmaFn pick_cols_tma(int n, bool inv);  // nullptr if none
 
 }  // namespace mp

@@ -29,9 +29,10 @@ MONC_PROJ_ESCRATCH = 7
 MONC_PROJ_NOALLOC_SCRATCH_BYTES = 32 << 20
 MONC_PROJ_FP64 = 0
 MONC_PROJ_MIXED = 1
+MONC_PROJ_REFINED = 2
 
-PRECISIONS = {"fp64": MONC_PROJ_FP64, "mixed": MONC_PROJ_MIXED}
-DTYPES = {MONC_PROJ_FP64: torch.float64, MONC_PROJ_MIXED: torch.float32}
+PRECISIONS = {"fp64": MONC_PROJ_FP64, "mixed": MONC_PROJ_MIXED, "refined": MONC_PROJ_REFINED}
+DTYPES = {MONC_PROJ_FP64: torch.float64, MONC_PROJ_MIXED: torch.float32, MONC_PROJ_REFINED: torch.float64}
 
 EXPORTS = [
     "monc_proj_plan", "monc_proj_workspace_size", "monc_proj_solve",

@@ -19,7 +19,7 @@ from paper_2009_12849_gb300 import workloads as W
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--grid", default="512,512,64")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "refined"])
     ap.add_argument("--solves", type=int, default=3)
     a = ap.parse_args()
     nx, ny, nz = (int(x) for x in a.grid.split(","))
