@@ -471,32 +471,43 @@ def measure_batch(dev, stream, count=64, reps=5):
         u, v, w = (torch.from_numpy(a).to(dev) for a in W.random_fields_f32(g, sd, False))
         args.append((u, v, w, torch.empty_like(u), torch.empty_like(v), torch.empty_like(w)))
     pts = sum(g.npoints for g in grids)
-    for _ in range(2):
-        B.solve(args, stream=stream)
-    torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        B.solve(args, stream=stream)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1) / reps
-    side = torch.cuda.Stream(dev)
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.stream(side):
-        with torch.cuda.graph(graph, stream=side):
-            B.solve(args, stream=side)
-    graph.replay()
-    torch.cuda.synchronize(dev)
-    e0.record(stream)
-    for _ in range(reps):
+
+    def timed():
+        for _ in range(2):
+            B.solve(args, stream=stream)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(reps):
+            B.solve(args, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        side = torch.cuda.Stream(dev)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph, stream=side):
+                B.solve(args, stream=side)
         graph.replay()
-    e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(reps):
+            graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return ms, e0.elapsed_time(e1) / reps
+
+    ms0, ms_graph0 = timed()
+    # task shapes picked per instance by the library's autotuner, then timed again
+    shapes = B.autotune(args, stream=stream)
     torch.cuda.synchronize(dev)
-    ms_graph = e0.elapsed_time(e1) / reps
+    ms, ms_graph = timed()
     B.close()
+    tuned = sorted({tuple(x) for x in shapes})
     return {"instances": count, "points": pts, "ms_per_batch": ms, "mpts_per_s": pts / (ms * 1e-3) / 1e6,
-            "graph_ms_per_batch": ms_graph, "graph_mpts_per_s": pts / (ms_graph * 1e-3) / 1e6}
+            "graph_ms_per_batch": ms_graph, "graph_mpts_per_s": pts / (ms_graph * 1e-3) / 1e6,
+            "autotuned": True, "shapes_kept": [list(x) for x in tuned],
+            "default_shapes": {"ms_per_batch": ms0, "graph_ms_per_batch": ms_graph0}}
 
 
 def accuracy_check(g, u_h, v_h, w_h, outs):

@@ -232,6 +232,30 @@ int monc_proj_solve_noalloc(int nx, int ny, int nz, double dx, double dy,
                             int precision, const void* u, const void* v, const void* w,
                             void* u_out, void* v_out, void* w_out, void* phi_out, void* stream);
 
+/*
+ * monc_proj_autotune -- pick the plan's task shapes by timing them (a tuning
+ * step with no counterpart in the paper).
+ *
+ * For compile-time transform lengths the row kernels take tasks of 32, 64 or
+ * 128 threads and the column kernels tiles of 128, 256 or 512 threads (the
+ * candidates whose shared memory fits).  Each distinct candidate runs one
+ * warm-up solve and `reps` timed solves (3 if reps <= 0) of the caller's
+ * fields on `stream`, timed with CUDA events; the fastest is kept in the plan.
+ * The call waits for the stream.  The solves write u_out, v_out, w_out (they
+ * may alias the inputs only if the inputs may be overwritten).  The shapes
+ * decide how the work is split into blocks, never the arithmetic, so the
+ * results are bitwise the same with every choice.  The call changes the plan:
+ * make it before the plan is shared between threads or solves are captured
+ * into a graph.  Plans running an opt-in kernel variant, or with run-time
+ * lengths both ways, keep their shapes.
+ *   row_threads, col_threads  host, nullable: the shapes kept
+ * Errors: EINVAL for NULL plan, field or workspace pointers; the first failing
+ * solve's status (the plan then keeps the shapes it had).
+ */
+int monc_proj_autotune(monc_proj_plan_t plan, const void* u, const void* v, const void* w, void* u_out,
+                       void* v_out, void* w_out, void* workspace, int reps, void* stream, int* row_threads,
+                       int* col_threads);
+
 /* Plan introspection: grid sizes, precision and the FP64-column count of a3. */
 int monc_proj_plan_info(monc_proj_plan_t plan, int* nx, int* ny, int* nz, int* precision,
                         long long* fp64_columns, long long* total_columns);

@@ -44,6 +44,7 @@ struct monc_proj_plan_s {
     bool ct_rows;                         // compile-time length along x
     bool ct_cols;                         // compile-time length along y
     bool fused;                           // square compile-time grid: fused persistent kernels
+    int row_threads, col_threads;         // threads of a compile-time row task / column tile
     int refine_passes;                    // MONC_PROJ_REFINED: passes per solve
     bool tma_cols;                        // FP32 compile-time column lengths: TMA-staged column kernels
     size_t smem_tma;                      // their dynamic shared memory (two tile buffers)
@@ -552,6 +553,61 @@ struct TableOffsets {
 
 // Fill the host-side part of a plan (sizes, radix plans, task shapes,
 // workspace layout) and build its device tables in `blob` (host memory).
+// Task shapes of the row and column kernels.  Compile-time lengths: one
+// shared buffer, blocks of p->row_threads (rows) or p->col_threads (column
+// tiles) threads x E elements (E = the largest radix: 32 FP32, 16 FP64);
+// monc_proj_autotune searches these two counts.  Run-time lengths: two
+// buffers (ping-pong) within ~96 KB, 256 threads.  The shapes decide how work
+// is split into blocks, never the arithmetic of a transform, so every choice
+// gives bitwise the same result.
+void set_task_shapes(monc_proj_plan_s* p) {
+    const int nx = p->nx, ny = p->ny;
+    const bool fp64 = p->precision == MONC_PROJ_FP64;
+    const size_t csz = fp64 ? 16 : 8;
+    const bool ctx = p->ct_rows, cty = p->ct_cols;
+    const int E = fp64 ? kMaxRadixF64 : kMaxRadixF32;
+    p->bs_row = spad_len(nx);
+    // column tiles: a pitch of 4 (mod 16) complex elements spreads the
+    // columns of a tile over distinct shared-memory banks
+    p->bs_col = spad_len(ny);
+    while (p->bs_col % 16 != 4) ++p->bs_col;
+    const size_t budget = 96 * 1024;
+    int npair = ctx ? std::max(1, std::min(16, p->row_threads * E / nx))
+                    : (int)std::max<size_t>(1, std::min<size_t>(8, budget / (2 * (size_t)p->bs_row * csz)));
+    npair = std::min(npair, (ny + 1) / 2);
+    p->rows_fwd = 2 * npair;
+    p->nrb_fwd = (ny + p->rows_fwd - 1) / p->rows_fwd;
+    p->thr_fwd_rows = ctx ? threads_for(npair * nx, E) : 256;
+    p->smem_fwd_rows = (size_t)(ctx ? 1 : 2) * npair * p->bs_row * csz;
+    int tw = cty ? std::max(1, std::min(32, p->col_threads * E / ny))
+                 : (int)std::max<size_t>(1, std::min<size_t>(8, budget / (2 * (size_t)p->bs_col * csz)));
+    tw = std::min(tw, p->nxh);
+    p->tw_cols = tw;
+    p->ntiles = (p->nxh + tw - 1) / tw;
+    p->thr_cols = cty ? threads_for(tw * ny, E) : 256;
+    p->smem_cols = (size_t)(cty ? 1 : 2) * tw * p->bs_col * csz;
+    p->smem_fcols = p->smem_cols;
+    // inverse row tasks: pairs of rows, one complex transform per channel and
+    // row pair; index 0 without phi output (3 channels), 1 with (4 channels)
+    for (int idx = 0; idx < 2; ++idx) {
+        const int nch = 3 + idx;
+        int pairs = std::max(1, npair / nch);
+        pairs = std::min(pairs, (ny + 1) / 2);
+        const int np = nch * pairs;
+        p->rows_inv[idx] = 2 * pairs;
+        p->thr_inv_rows[idx] = ctx ? threads_for(np * nx, E) : 256;
+        p->smem_inv_rows[idx] = (size_t)(ctx ? 1 : 2) * np * p->bs_row * csz;
+        if (ctx) {
+            // one channel per task: rows_inv rows = rows_inv/2 transforms
+            int npr = std::max(1, std::min({16, p->row_threads * E / nx, (ny + 1) / 2}));
+            p->rows_inv[idx] = 2 * npr;
+            p->thr_inv_rows[idx] = threads_for(npr * nx, E);
+            p->smem_inv_rows[idx] = (size_t)npr * p->bs_row * csz;
+        }
+    }
+
+}
+
 void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double dy,
                   const double* dz, const double* rho_c, const double* rho_f, int precision,
                   std::vector<unsigned char>& blob, TableOffsets& to) {
@@ -661,32 +717,13 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     to.err = blob.size();
     blob.resize(blob.size() + 256, 0);
 
-    // ---- task shapes.  Compile-time lengths: one shared buffer, blocks of
-    // kRowTaskThreads (rows) or kColTaskThreads (column tiles) threads x E
-    // elements (E = the largest radix: 32 FP32, 16 FP64).  Run-time lengths:
-    // two buffers (ping-pong) within ~96 KB, 256 threads.
-    const int E = fp64 ? kMaxRadixF64 : kMaxRadixF32;
-    p->bs_row = spad_len(nx);
-    // column tiles: a pitch of 4 (mod 16) complex elements spreads the
-    // columns of a tile over distinct shared-memory banks
-    p->bs_col = spad_len(ny);
-    while (p->bs_col % 16 != 4) ++p->bs_col;
-    const size_t budget = 96 * 1024;
-    int npair = ctx ? std::max(1, std::min(16, kRowTaskThreads * E / nx))
-                    : (int)std::max<size_t>(1, std::min<size_t>(8, budget / (2 * (size_t)p->bs_row * csz)));
-    npair = std::min(npair, (ny + 1) / 2);
-    p->rows_fwd = 2 * npair;
-    p->nrb_fwd = (ny + p->rows_fwd - 1) / p->rows_fwd;
-    p->thr_fwd_rows = ctx ? threads_for(npair * nx, E) : 256;
-    p->smem_fwd_rows = (size_t)(ctx ? 1 : 2) * npair * p->bs_row * csz;
-    int tw = cty ? std::max(1, std::min(32, kColTaskThreads * E / ny))
-                 : (int)std::max<size_t>(1, std::min<size_t>(8, budget / (2 * (size_t)p->bs_col * csz)));
-    tw = std::min(tw, p->nxh);
-    p->tw_cols = tw;
-    p->ntiles = (p->nxh + tw - 1) / tw;
-    p->thr_cols = cty ? threads_for(tw * ny, E) : 256;
-    p->smem_cols = (size_t)(cty ? 1 : 2) * tw * p->bs_col * csz;
-    p->smem_fcols = p->smem_cols;
+    p->ct_rows = ctx;
+    p->ct_cols = cty;
+    p->row_threads = kRowTaskThreads;
+    p->col_threads = kColTaskThreads;
+    set_task_shapes(p);
+    const int npair = p->rows_fwd / 2;
+    const int tw = p->tw_cols;
     // the persistent inverse column kernel (opt-in) holds two input stages
     // of ny x tw values plus the FFT buffer
     p->persist_cols = cty && ct_core_length(ny, fp64) && precision != MONC_PROJ_REFINED && persist_cols_enabled();
@@ -696,27 +733,6 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     p->tma_cols = !fp64 && cty && ct_core_length(ny, fp64) && precision != MONC_PROJ_REFINED && !p->persist_cols && (tw * csz) % 16 == 0 && p->smem_tma <= kSmemMax &&
                   tma_enabled() && tmap_encoder() != nullptr;
     if (p->persist_cols) p->smem_cols = ((size_t)2 * ny * tw + (size_t)tw * p->bs_col) * csz;
-    p->ct_rows = ctx;
-    p->ct_cols = cty;
-    // inverse row tasks: pairs of rows, one complex transform per channel and
-    // row pair; index 0 without phi output (3 channels), 1 with (4 channels)
-    for (int idx = 0; idx < 2; ++idx) {
-        const int nch = 3 + idx;
-        int pairs = std::max(1, npair / nch);
-        pairs = std::min(pairs, (ny + 1) / 2);
-        const int np = nch * pairs;
-        p->rows_inv[idx] = 2 * pairs;
-        p->thr_inv_rows[idx] = ctx ? threads_for(np * nx, E) : 256;
-        p->smem_inv_rows[idx] = (size_t)(ctx ? 1 : 2) * np * p->bs_row * csz;
-        if (ctx) {
-            // one channel per task: rows_inv rows = rows_inv/2 transforms
-            int npr = std::max(1, std::min({16, kRowTaskThreads * E / nx, (ny + 1) / 2}));
-            p->rows_inv[idx] = 2 * npr;
-            p->thr_inv_rows[idx] = threads_for(npr * nx, E);
-            p->smem_inv_rows[idx] = (size_t)npr * p->bs_row * csz;
-        }
-    }
-
     // fused persistent kernels for square compile-time grids: one block size
     // and shared-memory size for both task kinds of each kernel
     p->fused = ctx && cty && nx == ny && ct_core_length(nx, fp64) && precision != MONC_PROJ_REFINED &&
@@ -992,6 +1008,86 @@ int monc_proj_destroy(monc_proj_plan_t plan) {
     if (dev != plan->device && dev >= 0) cudaSetDevice(dev);
     delete plan;
     return MONC_PROJ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuning of the task shapes (no counterpart in the paper).
+// ---------------------------------------------------------------------------
+namespace {
+bool shapes_fit(const monc_proj_plan_s* p) {
+    const size_t lim = kSmemMax;
+    return p->thr_fwd_rows <= 512 && p->thr_cols <= 512 && p->thr_inv_rows[0] <= 512 && p->thr_inv_rows[1] <= 512 &&
+           p->smem_fwd_rows <= lim && p->smem_cols <= lim && p->smem_inv_rows[0] <= lim && p->smem_inv_rows[1] <= lim;
+}
+int apply_shapes(monc_proj_plan_s* p, int rt, int ct) {
+    p->row_threads = rt;
+    p->col_threads = ct;
+    set_task_shapes(p);
+    p->smem_fcols = p->smem_cols;
+    if (!shapes_fit(p)) return MONC_PROJ_EUNSUPPORTED;
+    return p->precision == MONC_PROJ_FP64 ? set_kernel_attrs<double>(p) : set_kernel_attrs<float>(p);
+}
+}  // namespace
+
+int monc_proj_autotune(monc_proj_plan_t plan, const void* u, const void* v, const void* w, void* u_out,
+                       void* v_out, void* w_out, void* workspace, int reps, void* stream, int* row_threads,
+                       int* col_threads) {
+    if (!plan || !u || !v || !w || !u_out || !v_out || !w_out || !workspace) return MONC_PROJ_EINVAL;
+    const int r0 = plan->row_threads, c0 = plan->col_threads;
+    auto report = [&](int rc) {
+        if (row_threads) *row_threads = plan->row_threads;
+        if (col_threads) *col_threads = plan->col_threads;
+        return rc;
+    };
+    if (plan->fused || plan->persist_cols || plan->tma_cols || (!plan->ct_rows && !plan->ct_cols))
+        return report(MONC_PROJ_OK);
+    if (reps <= 0) reps = 3;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        return report(MONC_PROJ_ECUDA);
+    }
+    const int rts[] = {32, 64, 128};
+    const int cts[] = {128, 256, 512};
+    float best = INFINITY;
+    int br = r0, bc = c0;
+    int rc = MONC_PROJ_OK;
+    std::vector<std::pair<int, int>> seen;      // (rows per forward task, columns per tile) tried
+    for (int rt : rts) {
+        if (!plan->ct_rows && rt != r0) continue;
+        for (int ct : cts) {
+            if (!plan->ct_cols && ct != c0) continue;
+            if (apply_shapes(plan, rt, ct) != MONC_PROJ_OK) continue;
+            const std::pair<int, int> key(plan->rows_fwd, plan->tw_cols);
+            if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
+            seen.push_back(key);
+            rc = monc_proj_solve(plan, u, v, w, u_out, v_out, w_out, nullptr, workspace, stream);
+            if (rc != MONC_PROJ_OK) break;
+            cudaEventRecord(e0, st);
+            for (int i = 0; i < reps && rc == MONC_PROJ_OK; ++i)
+                rc = monc_proj_solve(plan, u, v, w, u_out, v_out, w_out, nullptr, workspace, stream);
+            cudaEventRecord(e1, st);
+            if (rc != MONC_PROJ_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+                if (rc == MONC_PROJ_OK) rc = MONC_PROJ_ECUDA;
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                br = rt;
+                bc = ct;
+            }
+        }
+        if (rc != MONC_PROJ_OK) break;
+    }
+    cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const int ra = apply_shapes(plan, rc == MONC_PROJ_OK ? br : r0, rc == MONC_PROJ_OK ? bc : c0);
+    return report(rc != MONC_PROJ_OK ? rc : ra);
 }
 
 int monc_proj_plan_info(monc_proj_plan_t plan, int* nx, int* ny, int* nz, int* precision,

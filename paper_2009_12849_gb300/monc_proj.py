@@ -39,7 +39,7 @@ EXPORTS = [
     "monc_proj_batch_workspace_size", "monc_proj_solve_batch", "monc_proj_sync_status",
     "monc_proj_destroy", "monc_proj_status_string", "monc_proj_plan_info",
     "monc_proj_profile", "monc_proj_profile_read", "monc_proj_phase_name",
-    "monc_proj_solve_noalloc",
+    "monc_proj_solve_noalloc", "monc_proj_autotune",
 ]
 
 
@@ -86,6 +86,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.monc_proj_phase_name.argtypes = [i]
     L.monc_proj_phase_name.restype = ctypes.c_char_p
     L.monc_proj_solve_noalloc.argtypes = [i, i, i, d, d, dp, dp, dp, i, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.monc_proj_autotune.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i, vp, ip, ip]
     for name in EXPORTS:
         if name not in ("monc_proj_status_string", "monc_proj_phase_name"):
             getattr(L, name).restype = ctypes.c_int
@@ -143,6 +144,18 @@ def monc_proj_solve(plan: int, u, v, w, u_out, v_out, w_out, phi_out, workspace,
                                         ptr(v_out), ptr(w_out), ptr(phi_out), ptr(workspace),
                                         ctypes.c_void_p(_stream_handle(stream)))
     _check(rc, "monc_proj_solve")
+
+
+def monc_proj_autotune(plan: int, u, v, w, u_out, v_out, w_out, workspace, reps=3, stream=None):
+    """Time the plan's candidate task shapes on these fields and keep the
+    fastest; returns (row_threads, col_threads)."""
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+    rt, ct = ctypes.c_int(), ctypes.c_int()
+    _check(load_library().monc_proj_autotune(ctypes.c_void_p(plan), ptr(u), ptr(v), ptr(w), ptr(u_out),
+                                             ptr(v_out), ptr(w_out), ptr(workspace), int(reps),
+                                             ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(rt),
+                                             ctypes.byref(ct)), "monc_proj_autotune")
+    return rt.value, ct.value
 
 
 def monc_proj_batch_workspace_size(plans) -> int:
@@ -262,6 +275,12 @@ class Projector:
         monc_proj_solve(self.plan, u, v, w, out[0], out[1], out[2], p, self.workspace, stream)
         return (*out, p) if p is not None else tuple(out)
 
+    def autotune(self, u, v, w, reps=3, stream=None):
+        """Pick the plan's task shapes by timing them on (u, v, w), which
+        are left unchanged; returns (row_threads, col_threads)."""
+        out = (torch.empty_like(u), torch.empty_like(v), torch.empty_like(w))
+        return monc_proj_autotune(self.plan, u, v, w, *out, self.workspace, reps, stream)
+
     def sync_status(self, stream=None) -> int:
         return monc_proj_sync_status(self.plan, stream)
 
@@ -322,6 +341,16 @@ class BatchProjector:
             raise ProjError(MONC_PROJ_EINVAL, "BatchProjector.solve")
         full = [tuple(f) + (None,) * (7 - len(f)) for f in fields]
         monc_proj_solve_batch([p.handle for p in self.plans], full, self.workspace, stream)
+
+    def autotune(self, fields, reps=3, stream=None):
+        """Tune each instance's plan alone on its fields (inputs left
+        unchanged); returns the (row_threads, col_threads) kept per plan."""
+        out = []
+        for p, f in zip(self.plans, fields):
+            u, v, w = f[0], f[1], f[2]
+            tmp = (torch.empty_like(u), torch.empty_like(v), torch.empty_like(w))
+            out.append(monc_proj_autotune(p.handle, u, v, w, *tmp, self.workspace, reps, stream))
+        return out
 
     def close(self):
         for p in self.plans:

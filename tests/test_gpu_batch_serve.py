@@ -104,3 +104,26 @@ def test_admission_respects_budget():
     assert stats["max_inflight"] <= 2
     assert stats["peak_hbm_gb"] <= stats["hbm_budget_gb"]
     srv.close()
+
+
+@pytest.mark.parametrize("shape", [(256, 192, 8), (384, 480, 4), (96, 1024, 3)])
+def test_autotune_keeps_results_bitwise(shape):
+    """The autotuner changes how work is split into blocks, never the
+    arithmetic: results before and after tuning are bitwise equal, and the
+    shapes kept are among the candidates."""
+    import torch
+    mp = _mp()
+    nx, ny, nz = shape
+    g = W.make_grid(nx, ny, nz, 25.0, 20.0, W.geometric_dz(nz, 10.0, 100.0))
+    dev = torch.device("cuda", 0)
+    u, v, w = (torch.from_numpy(a).to(dev) for a in W.random_fields_f32(g, 3, True))
+    P = mp.Projector.from_grid(g, "mixed", dev)
+    ref = [x.clone() for x in P.solve(u, v, w, phi=True)]
+    rt, ct = P.autotune(u, v, w, reps=2)
+    assert rt in (32, 64, 128) and ct in (128, 256, 512)
+    got = P.solve(u, v, w, phi=True)
+    torch.cuda.synchronize()
+    assert P.sync_status() == 0
+    for a, b in zip(ref, got):
+        assert torch.equal(a, b)
+    P.close()
