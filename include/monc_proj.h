@@ -126,6 +126,29 @@ int monc_proj_solve(monc_proj_plan_t plan, const void* u, const void* v, const v
                     void* u_out, void* v_out, void* w_out, void* phi_out,
                     void* workspace, void* stream);
 
+/*
+ * One projection of host arrays: the fields are copied to a caller-owned
+ * device staging area, projected there in place, and copied back, all
+ * enqueued on `stream` (one cudaMemcpyAsync per array); the call returns
+ * without waiting.  Host buffers should be page-locked for the copies to run
+ * asynchronously (pageable ones make the copies wait on the host).  Two
+ * solves on different streams with different staging areas and workspaces
+ * overlap one's copies in with the other's copies out.
+ *
+ *   u, v, w            host, shapes and element type as in monc_proj_solve
+ *   u_out, v_out, w_out host, same shapes (may be the input buffers)
+ *   phi_out            host [nz][ny][nx] or NULL
+ *   staging            device, >= monc_proj_host_staging_size(plan, phi_out != NULL)
+ *                      bytes, 256-byte aligned
+ *   workspace          as in monc_proj_solve
+ * Errors: EINVAL for NULL plan, field, staging or workspace pointers or a
+ * short staging area; ECUDA if a copy cannot be enqueued.
+ */
+int monc_proj_host_staging_size(monc_proj_plan_t plan, int with_phi, size_t* bytes);
+int monc_proj_solve_host(monc_proj_plan_t plan, const void* u, const void* v, const void* w,
+                         void* u_out, void* v_out, void* w_out, void* phi_out,
+                         void* staging, size_t staging_bytes, void* workspace, void* stream);
+
 /* One field set of a batched solve (device pointers, as in monc_proj_solve). */
 typedef struct {
     const void* u;

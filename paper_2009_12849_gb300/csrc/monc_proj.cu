@@ -885,6 +885,56 @@ int monc_proj_solve(monc_proj_plan_t plan, const void* u, const void* v, const v
     return run_solve(plan, q, st);
 }
 
+namespace {
+// element size of a plan's fields and the byte sizes of its arrays
+void field_layout(const monc_proj_plan_s* p, size_t* elem, size_t* cbytes, size_t* fbytes) {
+    *elem = p->precision == MONC_PROJ_MIXED ? sizeof(float) : sizeof(double);
+    *cbytes = (size_t)p->nz * p->ny * p->nx * *elem;          // u, v, phi
+    *fbytes = (size_t)(p->nz + 1) * p->ny * p->nx * *elem;    // w
+}
+}  // namespace
+
+int monc_proj_host_staging_size(monc_proj_plan_t plan, int with_phi, size_t* bytes) {
+    if (!plan || !bytes) return MONC_PROJ_EINVAL;
+    size_t e, c, f;
+    field_layout(plan, &e, &c, &f);
+    *bytes = align256(c) * 2 + align256(f) + (with_phi ? align256(c) : 0);
+    return MONC_PROJ_OK;
+}
+
+int monc_proj_solve_host(monc_proj_plan_t plan, const void* u, const void* v, const void* w,
+                         void* u_out, void* v_out, void* w_out, void* phi_out,
+                         void* staging, size_t staging_bytes, void* workspace, void* stream) {
+    if (!plan || !u || !v || !w || !u_out || !v_out || !w_out || !staging || !workspace) return MONC_PROJ_EINVAL;
+    size_t need = 0;
+    monc_proj_host_staging_size(plan, phi_out != nullptr, &need);
+    if (staging_bytes < need || (((uintptr_t)staging) & 255)) return MONC_PROJ_EINVAL;
+    size_t e, c, f;
+    field_layout(plan, &e, &c, &f);
+    unsigned char* d = (unsigned char*)staging;
+    unsigned char* du = d;
+    unsigned char* dv = du + align256(c);
+    unsigned char* dw = dv + align256(c);
+    unsigned char* dp = phi_out ? dw + align256(f) : nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(du, u, c, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(dv, v, c, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(dw, w, f, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        cudaGetLastError();
+        return MONC_PROJ_ECUDA;
+    }
+    const int rc = monc_proj_solve(plan, du, dv, dw, du, dv, dw, dp, workspace, stream);
+    if (rc != MONC_PROJ_OK) return rc;
+    if (cudaMemcpyAsync(u_out, du, c, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(v_out, dv, c, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(w_out, dw, f, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        (phi_out && cudaMemcpyAsync(phi_out, dp, c, cudaMemcpyDeviceToHost, st) != cudaSuccess)) {
+        cudaGetLastError();
+        return MONC_PROJ_ECUDA;
+    }
+    return MONC_PROJ_OK;
+}
+
 int monc_proj_batch_workspace_size(const monc_proj_plan_t* plans, int count, size_t* bytes) {
     if (!plans || !bytes || count < 0) return MONC_PROJ_EINVAL;
     size_t total = 0;

@@ -39,7 +39,7 @@ EXPORTS = [
     "monc_proj_batch_workspace_size", "monc_proj_solve_batch", "monc_proj_sync_status",
     "monc_proj_destroy", "monc_proj_status_string", "monc_proj_plan_info",
     "monc_proj_profile", "monc_proj_profile_read", "monc_proj_phase_name",
-    "monc_proj_solve_noalloc", "monc_proj_autotune",
+    "monc_proj_solve_noalloc", "monc_proj_autotune", "monc_proj_host_staging_size", "monc_proj_solve_host",
 ]
 
 
@@ -87,6 +87,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.monc_proj_phase_name.restype = ctypes.c_char_p
     L.monc_proj_solve_noalloc.argtypes = [i, i, i, d, d, dp, dp, dp, i, vp, vp, vp, vp, vp, vp, vp, vp]
     L.monc_proj_autotune.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i, vp, ip, ip]
+    L.monc_proj_host_staging_size.argtypes = [vp, i, ctypes.POINTER(sz)]
+    L.monc_proj_solve_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp, vp]
     for name in EXPORTS:
         if name not in ("monc_proj_status_string", "monc_proj_phase_name"):
             getattr(L, name).restype = ctypes.c_int
@@ -156,6 +158,24 @@ def monc_proj_autotune(plan: int, u, v, w, u_out, v_out, w_out, workspace, reps=
                                              ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(rt),
                                              ctypes.byref(ct)), "monc_proj_autotune")
     return rt.value, ct.value
+
+
+def monc_proj_host_staging_size(plan: int, with_phi=False) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().monc_proj_host_staging_size(ctypes.c_void_p(plan), int(bool(with_phi)), ctypes.byref(n)),
+           "monc_proj_host_staging_size")
+    return n.value
+
+
+def monc_proj_solve_host(plan: int, u, v, w, u_out, v_out, w_out, phi_out, staging, workspace, stream=None):
+    """Enqueue one projection of host tensors (page-locked for asynchronous
+    copies) through a device staging buffer."""
+    ptr = lambda t: ctypes.c_void_p(None if t is None else t.data_ptr())
+    rc = load_library().monc_proj_solve_host(ctypes.c_void_p(plan), ptr(u), ptr(v), ptr(w), ptr(u_out), ptr(v_out),
+                                             ptr(w_out), ptr(phi_out), ptr(staging),
+                                             ctypes.c_size_t(staging.numel() * staging.element_size()),
+                                             ptr(workspace), ctypes.c_void_p(_stream_handle(stream)))
+    _check(rc, "monc_proj_solve_host")
 
 
 def monc_proj_batch_workspace_size(plans) -> int:
@@ -274,6 +294,17 @@ class Projector:
             self._check_field(p, c, "phi")
         monc_proj_solve(self.plan, u, v, w, out[0], out[1], out[2], p, self.workspace, stream)
         return (*out, p) if p is not None else tuple(out)
+
+    def solve_host(self, u, v, w, out, staging=None, workspace=None, stream=None):
+        """Project host tensors (page-locked for asynchronous copies) into the
+        host tensors `out` through a device staging buffer (allocated here
+        if not given); returns out.  Enqueued on `stream`."""
+        if staging is None:
+            staging = torch.empty(max(monc_proj_host_staging_size(self.plan), 256), dtype=torch.uint8,
+                                  device=self.device)
+        ws = self.workspace if workspace is None else workspace
+        monc_proj_solve_host(self.plan, u, v, w, out[0], out[1], out[2], None, staging, ws, stream)
+        return out
 
     def autotune(self, u, v, w, reps=3, stream=None):
         """Pick the plan's task shapes by timing them on (u, v, w), which

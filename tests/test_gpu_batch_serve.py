@@ -127,3 +127,32 @@ def test_autotune_keeps_results_bitwise(shape):
     for a, b in zip(ref, got):
         assert torch.equal(a, b)
     P.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_host_buffer_solve_matches_device_solve(prec):
+    """monc_proj_solve_host (host arrays in and out through a device staging
+    area) gives bitwise the device solve's result, with and without phi."""
+    import torch
+    mp = _mp()
+    g = W.make_grid(96, 80, 10, 25.0, 25.0, W.geometric_dz(10, 10.0, 60.0))
+    dev = torch.device("cuda", 0)
+    dt = mp.DTYPES[mp.PRECISIONS[prec]]
+    hu, hv, hw = (torch.from_numpy(a).to(dt).pin_memory() for a in W.random_fields(g, 4, True))
+    P = mp.Projector.from_grid(g, prec, dev)
+    ref = P.solve(hu.to(dev), hv.to(dev), hw.to(dev), phi=True)
+    outs = tuple(torch.empty_like(x).pin_memory() for x in (hu, hv, hw, hu))
+    stg = torch.empty(mp.monc_proj_host_staging_size(P.plan, True), dtype=torch.uint8, device=dev)
+    mp.monc_proj_solve_host(P.plan, hu, hv, hw, *outs, stg, P.workspace)
+    torch.cuda.synchronize()
+    for a, b in zip(ref, outs):
+        assert torch.equal(a.cpu(), b)
+    out3 = tuple(torch.empty_like(x).pin_memory() for x in (hu, hv, hw))
+    P.solve_host(hu, hv, hw, out3)
+    torch.cuda.synchronize()
+    for a, b in zip(ref[:3], out3):
+        assert torch.equal(a.cpu(), b)
+    short = torch.empty(256, dtype=torch.uint8, device=dev)
+    with pytest.raises(mp.ProjError):
+        mp.monc_proj_solve_host(P.plan, hu, hv, hw, *out3, None, short, P.workspace)
+    P.close()
