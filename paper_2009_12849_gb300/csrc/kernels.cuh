@@ -219,19 +219,20 @@ __global__ void __launch_bounds__(512) k_fwd_rows(ProjParams p) {
 
     C* T = (C*)p.T;
     const int nxh = p.nxh;
-    const int tot2 = npair * nxh;
-    for (int t = threadIdx.x; t < tot2; t += blockDim.x) {
-        const int q = t / nxh;
-        const int kx = t - q * nxh;
+    for (int q = 0; q < npair; ++q) {
         const int j = j0 + 2 * q;
-        C z = res[q * bs + spad(kx)];
-        C zc = cconj(res[q * bs + spad(kx == 0 ? 0 : nx - kx)]);
-        C a = cscale(cadd(z, zc), (R)0.5);
-        C dd = csub(z, zc);
-        C b = cmk<R>((R)0.5 * dd.y, (R)-0.5 * dd.x);
-        const size_t o = ((size_t)k * ny + j) * p.nxp + kx;
-        if (j < ny) T[o] = a;
-        if (j + 1 < ny) T[o + p.nxp] = b;
+        if (j >= ny) break;
+        const C* rq = res + q * bs;
+        C* to = T + ((size_t)k * ny + j) * p.nxp;
+        const bool second = j + 1 < ny;
+        for (int kx = threadIdx.x; kx < nxh; kx += blockDim.x) {
+            const C z = rq[spad(kx)];
+            const C zc = cconj(rq[spad(kx == 0 ? 0 : nx - kx)]);
+            const C a = cscale(cadd(z, zc), (R)0.5);
+            const C dd = csub(z, zc);
+            to[kx] = a;
+            if (second) to[kx + p.nxp] = cmk<R>((R)0.5 * dd.y, (R)-0.5 * dd.x);
+        }
     }
 }
 
