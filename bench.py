@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batch measurement")
     ap.add_argument("--no-refined", action="store_true", help="skip the refinement (mixed passes on FP64 fields) leg")
+    ap.add_argument("--e2e-lanes", type=int, default=4,
+                    help="streams (each with its own staging area and workspace) taking turns in the e2e leg")
     ap.add_argument("--serve-requests", type=int, default=10000,
                     help="requests of the serving measurement (0 skips it; the full recipe is 10000)")
     return ap.parse_args()
@@ -296,35 +298,38 @@ def main():
 
     # ---- end to end through the C ABI with host buffers (monc_proj_solve_host):
     # every step copies its fields in from page-locked host memory, projects
-    # them and copies them back; two streams with their own staging areas and
-    # workspaces take alternate steps, so one step's copies back overlap the
+    # them and copies them back; --e2e-lanes streams with their own staging
+    # areas and workspaces take turns, so one step's copies back overlap the
     # next step's copies in
     uh = torch.from_numpy(u_h).pin_memory()
     vh = torch.from_numpy(v_h).pin_memory()
     wh = torch.from_numpy(w_h).pin_memory()
     lanes = []
-    for li in range(2):
+    nl = max(1, args.e2e_lanes)
+    for li in range(nl):
         outs_h = tuple(torch.empty_like(x).pin_memory() for x in (uh, vh, wh))
         stg = torch.empty(MP.monc_proj_host_staging_size(P.plan), dtype=torch.uint8, device=dev)
         ws = P.workspace if li == 0 else torch.empty_like(P.workspace)
         lanes.append((torch.cuda.Stream(dev), outs_h, stg, ws))
-    e2e_steps = max(2, min(args.steps, 10))
+    e2e_steps = max(2 * nl, min(args.steps, 10))
 
     def e2e_step(i):
-        s_, o_, stg_, ws_ = lanes[i % 2]
+        s_, o_, stg_, ws_ = lanes[i % nl]
         MP.monc_proj_solve_host(P.plan, uh, vh, wh, o_[0], o_[1], o_[2], None, stg_, ws_, s_)
 
-    for i in range(max(2, args.warmup)):
+    for i in range(max(nl, args.warmup)):
         e2e_step(i)
     torch.cuda.synchronize(dev)
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(lanes[0][0])
-    lanes[1][0].wait_event(e0)
+    for ln in lanes[1:]:
+        ln[0].wait_event(e0)
     for i in range(e2e_steps):
         e2e_step(i)
-    lanes[0][0].wait_stream(lanes[1][0])
+    for ln in lanes[1:]:
+        lanes[0][0].wait_stream(ln[0])
     e1.record(lanes[0][0])
     torch.cuda.synchronize(dev)
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
@@ -447,7 +452,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": world * npts / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
                 "h2d_bytes_per_step": field_bytes, "d2h_bytes_per_step": field_bytes,
-                "ms_per_step": e2e_ms, "api": "monc_proj_solve_host, 2 streams",
+                "ms_per_step": e2e_ms, "api": f"monc_proj_solve_host, {nl} streams",
                 "matches_device_solve": e2e_match},
         "clocks": clk,
         "gpu_launches": nsolves * len(phases),
