@@ -26,12 +26,15 @@ struct ProjParams {
     const float* acoef32;
     const float* csum32;
     const float* idzn32;
+    const float* rflo32;        // FP32 copies of rflo, rfhi (the forward rows of FP32 fields)
+    const float* rfhi32;
     double lam_fp64;            // mixed plans: |lambda| below which a column runs in FP64
     const double* lamx;         // [nxh]  2(cos(2 pi kx/nx) - 1)/dx^2
     const double* lamy;         // [ny]
     const void* ex;             // [nxh]  (exp(2 pi i kx/nx) - 1)/dx, storage precision
     const void* ey;             // [ny]
     double idx, idy;            // 1/dx, 1/dy
+    float idx32, idy32;
     double scale;               // 1/(nx ny)
     // fields
     const void* u; const void* v; const void* w;
@@ -111,10 +114,13 @@ __global__ void __launch_bounds__(512) k_fwd_rows(ProjParams p) {
     const F* v = (const F*)p.v;
     const F* w = (const F*)p.w;
     const size_t plane = (size_t)ny * nx;
-    const F sv = (F)p.svol[k];
-    const F rlo = (F)p.rflo[k];
-    const F rhi = (F)p.rfhi[k];
-    const F idx = (F)p.idx, idy = (F)p.idy;
+    // per-level coefficients in the field precision (FP32 fields read the
+    // FP32 tables: no FP64 conversions in the kernel)
+    constexpr bool f32 = sizeof(F) == 4;
+    const F sv = f32 ? (F)p.svol32[k] : (F)p.svol[k];
+    const F rlo = f32 ? (F)p.rflo32[k] : (F)p.rflo[k];
+    const F rhi = f32 ? (F)p.rfhi32[k] : (F)p.rfhi[k];
+    const F idx = f32 ? (F)p.idx32 : (F)p.idx, idy = f32 ? (F)p.idy32 : (F)p.idy;
 
     const C* res;
     if constexpr (NX > 0 && NX % 4 == 0 && sizeof(R) == 4 && sizeof(F) == 4) {

@@ -30,6 +30,7 @@ struct monc_proj_plan_s {
     const double* svol; const double* rflo; const double* rfhi;
     const double* acoef; const double* idzn; const double* csum;
     const float* svol32; const float* acoef32; const float* csum32; const float* idzn32;
+    const float* rflo32; const float* rfhi32;
     double lam_fp64;
     long long fp64_cols;
     const double* lamx; const double* lamy;
@@ -253,9 +254,11 @@ ProjParams make_params(const monc_proj_plan_s* p, const void* u, const void* v, 
     q.twx = p->twx; q.twy = p->twy;
     q.svol = p->svol; q.rflo = p->rflo; q.rfhi = p->rfhi; q.acoef = p->acoef; q.idzn = p->idzn;
     q.csum = p->csum; q.svol32 = p->svol32; q.acoef32 = p->acoef32; q.csum32 = p->csum32;
+    q.rflo32 = p->rflo32; q.rfhi32 = p->rfhi32;
     q.idzn32 = p->idzn32; q.lam_fp64 = p->lam_fp64;
     q.lamx = p->lamx; q.lamy = p->lamy; q.ex = p->ex; q.ey = p->ey;
     q.idx = 1.0 / p->dx; q.idy = 1.0 / p->dy;
+    q.idx32 = (float)q.idx; q.idy32 = (float)q.idy;
     q.scale = 1.0 / ((double)p->nx * (double)p->ny);
     q.u = u; q.v = v; q.w = w; q.uo = uo; q.vo = vo; q.wo = wo; q.phi = phi;
     unsigned char* b = (unsigned char*)ws;
@@ -548,7 +551,7 @@ int validate_grid(int nx, int ny, int nz, double dx, double dy, const double* dz
 
 // Offsets of the plan's device tables inside one contiguous blob.
 struct TableOffsets {
-    size_t twx, twy, sv, rl, rh, a, iz, cs, sv32, a32, cs32, iz32, lx, ly, ex, ey, err;
+    size_t twx, twy, sv, rl, rh, a, iz, cs, sv32, a32, cs32, iz32, rl32, rh32, lx, ly, ex, ey, err;
 };
 
 // Fill the host-side part of a plan (sizes, radix plans, task shapes,
@@ -703,6 +706,8 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     to.iz = blob.size(); push_doubles(blob, idzn); pad_blob(blob);
     to.cs = blob.size(); push_doubles(blob, csum); pad_blob(blob);
     to.sv32 = blob.size(); push_floats(blob, svol); pad_blob(blob);
+    to.rl32 = blob.size(); push_floats(blob, rflo); pad_blob(blob);
+    to.rh32 = blob.size(); push_floats(blob, rfhi); pad_blob(blob);
     to.a32 = blob.size(); push_floats(blob, acoef); pad_blob(blob);
     to.cs32 = blob.size(); push_floats(blob, csum); pad_blob(blob);
     to.iz32 = blob.size(); push_floats(blob, idzn); pad_blob(blob);
@@ -782,6 +787,7 @@ void plan_bind(monc_proj_plan_s* p, unsigned char* db, const TableOffsets& to) {
     p->csum = (const double*)(db + to.cs);
     p->svol32 = (const float*)(db + to.sv32); p->acoef32 = (const float*)(db + to.a32);
     p->csum32 = (const float*)(db + to.cs32); p->idzn32 = (const float*)(db + to.iz32);
+    p->rflo32 = (const float*)(db + to.rl32); p->rfhi32 = (const float*)(db + to.rh32);
     p->lamy = (const double*)(db + to.ly); p->ex = db + to.ex; p->ey = db + to.ey;
     p->err = (int*)(db + to.err);
 }
