@@ -360,6 +360,8 @@ def main():
         torch.cuda.synchronize(dev)
         ms64 = a0.elapsed_time(a1) / n64
         fp64 = {"value": npts / (ms64 * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms64, "steps": n64}
+        if not args.no_check and rank == 0:
+            fp64["accuracy"] = accuracy_check(g, u_h, v_h, w_h, [x.cpu().numpy() for x in o64])
         P64.close()
         del o64
 
