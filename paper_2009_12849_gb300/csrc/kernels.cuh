@@ -212,8 +212,16 @@ __global__ void __launch_bounds__(512) k_fwd_rows(ProjParams p) {
                 if (t < tot) {
                     const int r = (NX > 0) ? t / NX : t / nx;
                     const int i = t - r * nx;
-                    const F hdiv = (uc[c] - um[c]) * idx + (vc[c] - vm[c]) * idy;
-                    const F d = sv * hdiv + (rhi * wh[c] - rlo * wl[c]);
+                    F d;
+                    if constexpr (sizeof(F) == 8 && sizeof(R) == 4) {
+                        // FP64 fields of the refinement passes: the same sum in
+                        // fused multiply-adds (FP64 arithmetic is this GPU's
+                        // scarce resource)
+                        d = fma(sv * idx, uc[c] - um[c], fma(sv * idy, vc[c] - vm[c], fma(rhi, wh[c], -rlo * wl[c])));
+                    } else {
+                        const F hdiv = (uc[c] - um[c]) * idx + (vc[c] - vm[c]) * idy;
+                        d = sv * hdiv + (rhi * wh[c] - rlo * wl[c]);
+                    }
                     R* slot = (R*)&bufA[(r >> 1) * bs + spad(i)];
                     slot[r & 1] = (R)d;
                 }
@@ -986,9 +994,9 @@ __global__ void __launch_bounds__(256) k_fd_correct(ProjParams p, const F* __res
         const F uu = u[row + i], vv = v[row + i];
         const F ww = (k > 0) ? w[row + i] : (F)0;
         const F pb = (k > 0) ? phi[row - plane + i] : (F)0;
-        uo[row + i] = uu - (pe - ph) * idx;
-        vo[row + i] = vv - (pn - ph) * idy;
-        wo[row + i] = (k > 0) ? ww - (ph - pb) * iz : (F)0;
+        uo[row + i] = fma(-idx, pe - ph, uu);
+        vo[row + i] = fma(-idy, pn - ph, vv);
+        wo[row + i] = (k > 0) ? fma(-iz, ph - pb, ww) : (F)0;
         if (k == nz - 1) wo[row + plane + i] = (F)0;
         if (phi_sum) {
             const F sum = accumulate ? phi_sum[row + i] + ph : ph;
