@@ -70,7 +70,9 @@ typedef enum {
     MONC_PROJ_ECUDA = 4,         /* a CUDA runtime call failed (launch, copy) */
     MONC_PROJ_ETIMEOUT = 5,      /* a bounded device wait gave up (latched device error) */
     MONC_PROJ_EDEVICE = 6,       /* another device-detected error (latched device error) */
-    MONC_PROJ_ESCRATCH = 7       /* monc_proj_solve_noalloc: problem too large for its static scratch */
+    MONC_PROJ_ESCRATCH = 7,      /* monc_proj_solve_noalloc: problem too large for its static scratch */
+    MONC_PROJ_ENOCONV = 8,       /* monc_proj_solve_krylov: iteration limit reached before the tolerance */
+    MONC_PROJ_EBREAKDOWN = 9     /* monc_proj_solve_krylov: a BiCGStab denominator was exactly zero */
 } monc_proj_status;
 
 typedef enum {
@@ -278,6 +280,56 @@ int monc_proj_solve_noalloc(int nx, int ny, int nz, double dx, double dy,
 int monc_proj_autotune(monc_proj_plan_t plan, const void* u, const void* v, const void* w, void* u_out,
                        void* v_out, void* w_out, void* workspace, int reps, void* stream, int* row_threads,
                        int* col_threads);
+
+/* ---------------------------------------------------------------------------
+ * Krylov pressure solve (paper, Section 4: the model's second pressure solver
+ * runs a Krylov subspace method, BiCGStab preconditioned by ILU, on the same
+ * Poisson problem; the closing section names a preconditioner built on the
+ * problem's structure as further work).
+ *
+ * Solves L phi = D(u*) with L = D o G (the operator of monc_proj_solve,
+ * written as its 7-point stencil) by BiCGStab from phi = 0, the
+ * preconditioner applied to the search directions:
+ *   MONC_PROJ_PC_NONE  none;
+ *   MONC_PROJ_PC_LINE  the vertical lines of L (its vertical rows plus the
+ *                      diagonal of its horizontal part): one Thomas solve per
+ *                      column (i, j), all columns in parallel.
+ * Stops when ||r||_2 <= tol ||b||_2 (b = D(u*), r the recurrence residual),
+ * tested after each half step and each full step.  Precision follows the
+ * plan: FP64 and REFINED plans run the vectors in FP64, MIXED plans in FP32
+ * (the paper's single-precision solver; GB300 runs FP32 arithmetic 64 times
+ * faster than FP64, and FP32 attains relative residuals down to about 1e-6).
+ * The iterate is accumulated in FP64 in both and the gradient G phi of the
+ * outputs formed in FP64.  The outputs are those of
+ * monc_proj_solve: u - G phi, phi pinned to a zero level-0 horizontal mean,
+ * w zero on the bottom and top faces.
+ *
+ *   plan        any plan; its precision sets the field type (FP32 for
+ *               MIXED, FP64 otherwise)
+ *   u .. phi_out  device arrays of that type laid out as for
+ *               monc_proj_solve, aligned to the element size; outputs may
+ *               alias the inputs; phi_out may be NULL
+ *   workspace   device, caller-owned, 256-byte aligned, at least
+ *               monc_proj_krylov_workspace_size bytes (one FP64 and seven
+ *               field-type arrays of nx*ny*nz values, and a few KB)
+ *   tol         >= 0 and finite (0: run max_iter iterations)
+ *   max_iter    >= 0
+ *   precond     MONC_PROJ_PC_NONE or MONC_PROJ_PC_LINE
+ *   iterations, rel_residual  host, nullable: iterations completed and the
+ *               final ||r||/||b|| (0 for a divergence-free input)
+ * Returns OK when converged; MONC_PROJ_ENOCONV at the iteration limit and
+ * MONC_PROJ_EBREAKDOWN when a BiCGStab denominator is exactly zero (in both
+ * cases the outputs hold the projection with the last iterate); EINVAL for a
+ * bad argument; ECUDA for a failed launch or copy.
+ * The calling thread waits on `stream` once per iteration (the convergence
+ * test reads the residual back), so the call cannot be captured into a graph.
+ */
+typedef enum { MONC_PROJ_PC_NONE = 0, MONC_PROJ_PC_LINE = 1 } monc_proj_precond_t;
+int monc_proj_krylov_workspace_size(monc_proj_plan_t plan, size_t* bytes);
+int monc_proj_solve_krylov(monc_proj_plan_t plan, const void* u, const void* v, const void* w,
+                           void* u_out, void* v_out, void* w_out, void* phi_out, void* workspace,
+                           double tol, int max_iter, int precond, int* iterations, double* rel_residual,
+                           void* stream);
 
 /* Plan introspection: grid sizes, precision and the FP64-column count of a3. */
 int monc_proj_plan_info(monc_proj_plan_t plan, int* nx, int* ny, int* nz, int* precision,

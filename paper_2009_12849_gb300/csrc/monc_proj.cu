@@ -15,6 +15,7 @@
 
 #include <cudaTypedefs.h>
 
+#include "krylov.h"
 #include "pickers.h"
 
 using namespace mp;
@@ -838,6 +839,8 @@ const char* monc_proj_status_string(int status) {
         case MONC_PROJ_ETIMEOUT: return "bounded device wait timed out";
         case MONC_PROJ_EDEVICE: return "device-detected error";
         case MONC_PROJ_ESCRATCH: return "problem too large for the no-alloc static scratch";
+        case MONC_PROJ_ENOCONV: return "Krylov solve reached its iteration limit";
+        case MONC_PROJ_EBREAKDOWN: return "Krylov solve broke down (zero denominator)";
         default: return "unknown status";
     }
 }
@@ -889,6 +892,44 @@ int monc_proj_solve(monc_proj_plan_t plan, const void* u, const void* v, const v
     ProjParams q = make_params(plan, u, v, w, u_out, v_out, w_out, phi_out, workspace);
     cudaStream_t st = (cudaStream_t)stream;
     return run_solve(plan, q, st);
+}
+
+int monc_proj_krylov_workspace_size(monc_proj_plan_t plan, size_t* bytes) {
+    if (!plan || !bytes) return MONC_PROJ_EINVAL;
+    *bytes = krylov_workspace_bytes(plan->nx, plan->ny, plan->nz, plan->nsm, plan->precision == MONC_PROJ_MIXED);
+    return MONC_PROJ_OK;
+}
+
+int monc_proj_solve_krylov(monc_proj_plan_t plan, const void* u, const void* v, const void* w,
+                           void* u_out, void* v_out, void* w_out, void* phi_out, void* workspace,
+                           double tol, int max_iter, int precond, int* iterations, double* rel_residual,
+                           void* stream) {
+    if (!plan || !u || !v || !w || !u_out || !v_out || !w_out || !workspace) return MONC_PROJ_EINVAL;
+    if (!(tol >= 0.0) || !std::isfinite(tol) || max_iter < 0) return MONC_PROJ_EINVAL;
+    if (precond != MONC_PROJ_PC_NONE && precond != MONC_PROJ_PC_LINE) return MONC_PROJ_EINVAL;
+    const bool fp32 = plan->precision == MONC_PROJ_MIXED;
+    const void* ptrs[] = {u, v, w, u_out, v_out, w_out, phi_out};
+    for (const void* x : ptrs)
+        if (((uintptr_t)x) & (fp32 ? 3 : 7)) return MONC_PROJ_EINVAL;
+    if (((uintptr_t)workspace) & 255) return MONC_PROJ_EINVAL;
+    KrylovProblem kp{};
+    kp.fp32 = fp32;
+    kp.nx = plan->nx; kp.ny = plan->ny; kp.nz = plan->nz; kp.nsm = plan->nsm;
+    kp.dx = plan->dx; kp.dy = plan->dy;
+    kp.acoef = plan->acoef; kp.svol = plan->svol; kp.rflo = plan->rflo; kp.rfhi = plan->rfhi;
+    kp.idzn = plan->idzn;
+    kp.u = u; kp.v = v; kp.w = w;
+    kp.u_out = u_out; kp.v_out = v_out; kp.w_out = w_out; kp.phi_out = phi_out;
+    kp.workspace = workspace;
+    kp.tol = tol; kp.max_iter = max_iter; kp.precond = precond;
+    KrylovResult res{};
+    if (krylov_run(kp, (cudaStream_t)stream, &res) != cudaSuccess) {
+        cudaGetLastError();
+        return MONC_PROJ_ECUDA;
+    }
+    if (iterations) *iterations = res.iterations;
+    if (rel_residual) *rel_residual = res.rel_residual;
+    return res.status == 0 ? MONC_PROJ_OK : res.status == 1 ? MONC_PROJ_ENOCONV : MONC_PROJ_EBREAKDOWN;
 }
 
 namespace {

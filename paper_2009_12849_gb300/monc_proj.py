@@ -26,6 +26,11 @@ MONC_PROJ_ECUDA = 4
 MONC_PROJ_ETIMEOUT = 5
 MONC_PROJ_EDEVICE = 6
 MONC_PROJ_ESCRATCH = 7
+MONC_PROJ_ENOCONV = 8
+MONC_PROJ_EBREAKDOWN = 9
+MONC_PROJ_PC_NONE = 0
+MONC_PROJ_PC_LINE = 1
+PRECONDITIONERS = {"none": MONC_PROJ_PC_NONE, "line": MONC_PROJ_PC_LINE}
 MONC_PROJ_NOALLOC_SCRATCH_BYTES = 32 << 20
 MONC_PROJ_FP64 = 0
 MONC_PROJ_MIXED = 1
@@ -40,6 +45,7 @@ EXPORTS = [
     "monc_proj_destroy", "monc_proj_status_string", "monc_proj_plan_info",
     "monc_proj_profile", "monc_proj_profile_read", "monc_proj_phase_name",
     "monc_proj_solve_noalloc", "monc_proj_autotune", "monc_proj_host_staging_size", "monc_proj_solve_host",
+    "monc_proj_krylov_workspace_size", "monc_proj_solve_krylov",
 ]
 
 
@@ -89,6 +95,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.monc_proj_autotune.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i, vp, ip, ip]
     L.monc_proj_host_staging_size.argtypes = [vp, i, ctypes.POINTER(sz)]
     L.monc_proj_solve_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp, vp]
+    L.monc_proj_krylov_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
+    L.monc_proj_solve_krylov.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, d, i, i, ip, dp, vp]
     for name in EXPORTS:
         if name not in ("monc_proj_status_string", "monc_proj_phase_name"):
             getattr(L, name).restype = ctypes.c_int
@@ -176,6 +184,31 @@ def monc_proj_solve_host(plan: int, u, v, w, u_out, v_out, w_out, phi_out, stagi
                                              ctypes.c_size_t(staging.numel() * staging.element_size()),
                                              ptr(workspace), ctypes.c_void_p(_stream_handle(stream)))
     _check(rc, "monc_proj_solve_host")
+
+
+def monc_proj_krylov_workspace_size(plan: int) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().monc_proj_krylov_workspace_size(ctypes.c_void_p(plan), ctypes.byref(n)),
+           "monc_proj_krylov_workspace_size")
+    return n.value
+
+
+def monc_proj_solve_krylov(plan: int, u, v, w, u_out, v_out, w_out, phi_out, workspace, tol, max_iter,
+                           precond="line", stream=None):
+    """BiCGStab projection of the plan's field type; returns (status, iterations,
+    relative residual).  Status OK, MONC_PROJ_ENOCONV or MONC_PROJ_EBREAKDOWN
+    is returned (the outputs are written in all three cases); any other
+    status raises."""
+    ptr = lambda t: ctypes.c_void_p(None if t is None else t.data_ptr())
+    pc = PRECONDITIONERS[precond] if isinstance(precond, str) else int(precond)
+    it, rr = ctypes.c_int(), ctypes.c_double()
+    rc = load_library().monc_proj_solve_krylov(ctypes.c_void_p(plan), ptr(u), ptr(v), ptr(w), ptr(u_out),
+                                               ptr(v_out), ptr(w_out), ptr(phi_out), ptr(workspace),
+                                               float(tol), int(max_iter), pc, ctypes.byref(it), ctypes.byref(rr),
+                                               ctypes.c_void_p(_stream_handle(stream)))
+    if rc not in (MONC_PROJ_OK, MONC_PROJ_ENOCONV, MONC_PROJ_EBREAKDOWN):
+        raise ProjError(rc, "monc_proj_solve_krylov")
+    return rc, it.value, rr.value
 
 
 def monc_proj_batch_workspace_size(plans) -> int:
@@ -305,6 +338,31 @@ class Projector:
         ws = self.workspace if workspace is None else workspace
         monc_proj_solve_host(self.plan, u, v, w, out[0], out[1], out[2], None, staging, ws, stream)
         return out
+
+    def solve_krylov(self, u, v, w, tol=1e-4, max_iter=1000, precond="line", out=None, phi=False,
+                     workspace=None, stream=None):
+        """Project (u, v, w) with the BiCGStab pressure solver (FP32 vectors
+        for mixed plans, FP64 otherwise); returns (u_out, v_out, w_out, phi or None, status, iterations,
+        relative residual).  The Krylov workspace is allocated here unless
+        given."""
+        c = (self.nz, self.ny, self.nx)
+        f = (self.nz + 1, self.ny, self.nx)
+        self._check_field(u, c, "u")
+        self._check_field(v, c, "v")
+        self._check_field(w, f, "w")
+        if out is None:
+            out = (torch.empty_like(u), torch.empty_like(v), torch.empty_like(w))
+        for t, s, n in zip(out, (c, c, f), ("u_out", "v_out", "w_out")):
+            self._check_field(t, s, n)
+        p = torch.empty(c, dtype=self.dtype, device=self.device) if phi is True else (phi or None)
+        if p is not None:
+            self._check_field(p, c, "phi")
+        if workspace is None:
+            workspace = torch.empty(max(monc_proj_krylov_workspace_size(self.plan), 256), dtype=torch.uint8,
+                                    device=self.device)
+        st, it, rr = monc_proj_solve_krylov(self.plan, u, v, w, out[0], out[1], out[2], p, workspace, tol,
+                                            max_iter, precond, stream)
+        return (*out, p, st, it, rr)
 
     def autotune(self, u, v, w, reps=3, stream=None):
         """Pick the plan's task shapes by timing them on (u, v, w), which
