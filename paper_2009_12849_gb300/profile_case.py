@@ -1,9 +1,12 @@
 """Run a few projections of one synthetic grid, for profiling under ncu.
 
     python -m paper_2009_12849_gb300.profile_case --grid 512,512,64 --precision mixed --solves 3
+    python -m paper_2009_12849_gb300.profile_case --grid 256,256,128 --krylov 3
 
 Inputs are the seeded workload recipe (N(0,1) plus the large-scale mode,
 dx = dy = 10 m, dz geometric 5 -> 50 m).  Prints the wall time per solve.
+With --krylov N each solve is N BiCGStab iterations (vertical-line
+preconditioner, no stopping test) instead of the FFT projection.
 """
 from __future__ import annotations
 
@@ -21,6 +24,7 @@ def main():
     ap.add_argument("--grid", default="512,512,64")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "refined"])
     ap.add_argument("--solves", type=int, default=3)
+    ap.add_argument("--krylov", type=int, default=0, help="BiCGStab iterations per solve (0: FFT solve)")
     a = ap.parse_args()
     nx, ny, nz = (int(x) for x in a.grid.split(","))
     g = W.make_grid(nx, ny, nz, 10.0, 10.0, W.geometric_dz(nz, 5.0, 50.0))
@@ -29,14 +33,21 @@ def main():
     u, v, w = (torch.from_numpy(x).to(dev, dt) for x in W.random_fields_f32(g, 2, True))
     P = MP.Projector.from_grid(g, a.precision, dev)
     out = (torch.empty_like(u), torch.empty_like(v), torch.empty_like(w))
+    ws = None
+    if a.krylov > 0:
+        ws = torch.empty(MP.monc_proj_krylov_workspace_size(P.plan), dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(a.solves):
-        P.solve(u, v, w, out=out)
+        if a.krylov > 0:
+            P.solve_krylov(u, v, w, 0.0, a.krylov, "line", out=out, workspace=ws)
+        else:
+            P.solve(u, v, w, out=out)
     torch.cuda.synchronize()
     dt_s = (time.perf_counter() - t0) / a.solves
     st = P.sync_status()
-    print(f"{nx}x{ny}x{nz} {a.precision}: {dt_s * 1e3:.3f} ms/solve (wall), status {st}")
+    kind = f" krylov x{a.krylov}" if a.krylov > 0 else ""
+    print(f"{nx}x{ny}x{nz} {a.precision}{kind}: {dt_s * 1e3:.3f} ms/solve (wall), status {st}")
     if st != 0:
         raise SystemExit(1)
 
