@@ -72,7 +72,7 @@ def sample_grid(g, nlev):
 class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -81,14 +81,30 @@ class ClockSampler:
         self.proc = None
         self.path = os.path.join("/tmp", f"monc_clocks_{os.getpid()}.csv")
 
+    INTERVAL_MS = 50
+
     def start(self):
+        """Start sampling and wait (up to 5 s) for the first sample, so the
+        sampler is running when the timed region begins."""
+        self.window = None
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+                 "-lms", str(self.INTERVAL_MS)], stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t_end = time.time() + 5.0
+        while time.time() < t_end:
+            self.fh.flush()
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
+
+    def mark(self, t0: float, t1: float):
+        """Host times (time.time()) bracketing the timed region."""
+        self.window = (t0, t1)
 
     def stop(self):
         if self.proc is None:
@@ -99,23 +115,38 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        sm, smax, reasons = [], [], set()
+        import datetime
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[1]), float(parts[2]), parts[5:9]))
             except ValueError:
                 continue
-            for nm, val in zip(names, parts[5:9]):
+        # samples inside the timed region (plus one sampling interval either
+        # side); if it was too short to catch any, the nearest three
+        window = "timed region"
+        sel = rows
+        if self.window is not None and rows:
+            pad = self.INTERVAL_MS / 1000.0
+            sel = [r for r in rows if self.window[0] - pad <= r[0] <= self.window[1] + pad]
+            if not sel:
+                mid = 0.5 * (self.window[0] + self.window[1])
+                sel = sorted(rows, key=lambda r: abs(r[0] - mid))[:3]
+                window = "nearest samples"
+        reasons = set()
+        for r in sel:
+            for nm, val in zip(names, r[3]):
                 if val.lower().startswith("active"):
                     reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": statistics.median([r[1] for r in sel]) if sel else None,
+                "sm_max_mhz": max(r[2] for r in sel) if sel else None,
+                "reasons": sorted(reasons), "samples": len(sel), "window": window,
+                "interval_ms": self.INTERVAL_MS}
 
 
 # ------------------------------------------------------------------ roofline bookkeeping
@@ -275,16 +306,18 @@ def main():
 
     clocks = ClockSampler(local_rank)
     MP.monc_proj_profile(P.plan, True)
+    clocks.start()
     barrier()
     torch.cuda.synchronize(dev)
-    clocks.start()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    t_region0 = time.time()
     ev0.record(stream)
     for _ in range(args.steps):
         P.solve(u, v, w, out=out)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
+    clocks.mark(t_region0, time.time())
     barrier()
     clk = clocks.stop()
     MP.monc_proj_profile(P.plan, False)
