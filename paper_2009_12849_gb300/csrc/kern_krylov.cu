@@ -34,9 +34,10 @@
 // of a reducing kernel writes its partial sums; the last block to finish (a
 // ticket counter) adds all partials in a fixed order and forms the next
 // scalar, so results are deterministic run to run and no separate reduction
-// launch is needed.  The host reads the scalar block once per iteration to
-// test convergence; kernels of an iteration that has already stopped return
-// at once.  A denominator that is zero or not finite (rounding past the
+// launch is needed.  The host enqueues kKryCheckEvery iterations at a time
+// and then reads the scalar block to test convergence; the kernels of the
+// iterations after the one that stopped return at once, so the iteration
+// count and the result are those of a test after every iteration.  A denominator that is zero or not finite (rounding past the
 // attainable accuracy) ends the method as a breakdown.
 //
 // After the solve phi is pinned as in the FFT solver (level-0 horizontal mean
@@ -54,6 +55,7 @@ constexpr int kKryThreads = 256;
 constexpr int kKryBlocksPerSm = 8;       // streaming kernels: 2048 threads per SM
 constexpr int kKryIlp = 4;               // elements in flight per thread (streaming kernels)
 constexpr int kKrySums = 2;              // partial sums per block
+constexpr int kKryCheckEvery = 8;        // iterations enqueued between host convergence tests
 constexpr int kTileX = 32, kTileY = 8;   // stencil kernels: a 32 x 8 tile of columns
 constexpr int kTileZ = 8;                //   marching over 8 levels
 // line sweeps: levels loaded before use (32 FP32 or 16 FP64 values: about
@@ -571,6 +573,7 @@ cudaError_t run(const KrylovProblem& kp, cudaStream_t st, KrylovResult* res) {
     if ((e = cudaMemcpyAsync(&h, ws.sc, sizeof(KrySc), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
     for (int it = 1; it <= mi && !h.done; ++it) {
+        const bool check = (it % kKryCheckEvery == 0) || it == mi;
         k_kry_p<T><<<nblk, kKryThreads, 0, st>>>(g, ws.p, ws.r, ws.v, it == 1, ws.sc);
         if (pc) k_kry_line<T><<<cblk, kKryThreads, 0, st>>>(g, ws.tab, ws.p, ws.ph, ws.sc);
         k_kry_apply<T><<<sh.tiles, tb, 0, st>>>(g, ws.tab, ph, ws.v, ws.rt, false, rd(sh.ntile, kStAlpha, it));
@@ -580,6 +583,7 @@ cudaError_t run(const KrylovProblem& kp, cudaStream_t st, KrylovResult* res) {
         k_kry_update<T><<<nblk, kKryThreads, 0, st>>>(g, ws.xh, ws.xl, ph, shv, ws.r, ws.t, ws.rt,
                                                       rd(nblk, kStR, it));
         KRY_CHECK();
+        if (!check) continue;
         if ((e = cudaMemcpyAsync(&h, ws.sc, sizeof(KrySc), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
     }
