@@ -57,7 +57,8 @@ constexpr int kKryIlp = 4;               // elements in flight per thread (strea
 constexpr int kKrySums = 2;              // partial sums per block
 constexpr int kKryCheckEvery = 8;        // iterations enqueued between host convergence tests
 constexpr int kTileX = 32, kTileY = 8;   // stencil kernels: a 32 x 8 tile of columns
-constexpr int kTileZ = 8;                //   marching over 8 levels
+constexpr int kTileZ = 32;               //   marching over 32 levels (one reduction per block)
+constexpr int kApplyBatch = 8;           // FP32 stencil: levels whose operands load together
 // line sweeps: levels loaded before use (32 FP32 or 16 FP64 values: about
 // 128 bytes per thread in flight, enough to cover DRAM latency with the few
 // threads one per column gives)
@@ -325,15 +326,13 @@ __global__ void __launch_bounds__(kKryThreads) k_kry_rhs(Grid<T> g, Tabs<T> tb, 
 }
 
 // y = L x; partials: (a, y) and, if yy, (y, y).  (Stencil tiles.)  FP32:
-// every operand of the thread's kTileZ levels is loaded before the first is
-// used (64 registers); FP64 marches up the levels keeping the vertical
-// neighbours in registers (the batched form needs 118 registers and measured
-// slower).
+// the operands of kApplyBatch levels are loaded before the first is used;
+// FP64 marches up the levels keeping the vertical neighbours in registers
+// (the batched form needs 118 registers and measured slower).
 template <typename T>
 __global__ void __launch_bounds__(kKryThreads) k_kry_apply(Grid<T> g, Tabs<T> tb, const T* x, T* y, const T* a,
                                                            bool yy, Reduce rd) {
     if (rd.sc->done || rd.sc->half) return;
-    constexpr int Z = kTileZ;
     T s1 = 0, s2 = 0;
     Col cl;
     if constexpr (sizeof(T) == 8) {
@@ -354,33 +353,36 @@ __global__ void __launch_bounds__(kKryThreads) k_kry_apply(Grid<T> g, Tabs<T> tb
             }
         }
     } else if (tile_column(g, cl)) {
-        T xc[Z + 2], xe[Z], xw[Z], xn[Z], xs[Z], av[Z];
-        xc[0] = (cl.k0 > 0) ? x[(size_t)(cl.k0 - 1) * g.plane + cl.c] : (T)0;
+        constexpr int Zb = kApplyBatch;
+        for (int kb = cl.k0; kb < cl.k1; kb += Zb) {
+            T xc[Zb + 2], xe[Zb], xw[Zb], xn[Zb], xs[Zb], av[Zb];
+            xc[0] = (kb > 0) ? x[(size_t)(kb - 1) * g.plane + cl.c] : (T)0;
 #pragma unroll
-        for (int i = 0; i <= Z; ++i) {
-            const int k = cl.k0 + i;
-            xc[i + 1] = (k < g.nz) ? x[(size_t)k * g.plane + cl.c] : (T)0;
-        }
+            for (int i = 0; i <= Zb; ++i) {
+                const int k = kb + i;
+                xc[i + 1] = (k < g.nz) ? x[(size_t)k * g.plane + cl.c] : (T)0;
+            }
 #pragma unroll
-        for (int i = 0; i < Z; ++i) {
-            const int k = cl.k0 + i;
-            const size_t o = (size_t)(k < cl.k1 ? k : cl.k0) * g.plane;
-            xe[i] = x[o + cl.ce];
-            xw[i] = x[o + cl.cw];
-            xn[i] = x[o + cl.cn];
-            xs[i] = x[o + cl.cs];
-            av[i] = a[o + cl.c];
-        }
+            for (int i = 0; i < Zb; ++i) {
+                const int k = kb + i;
+                const size_t o = (size_t)(k < cl.k1 ? k : kb) * g.plane;
+                xe[i] = x[o + cl.ce];
+                xw[i] = x[o + cl.cw];
+                xn[i] = x[o + cl.cn];
+                xs[i] = x[o + cl.cs];
+                av[i] = a[o + cl.c];
+            }
 #pragma unroll
-        for (int i = 0; i < Z; ++i) {
-            const int k = cl.k0 + i;
-            if (k < cl.k1) {
-                const T c = xc[i + 1];
-                const T o1 = (xe[i] - (T)2 * c + xw[i]) * g.idx2 + (xn[i] - (T)2 * c + xs[i]) * g.idy2 +
-                             tb.vdiag[k] * c + tb.vsub[k] * xc[i] + tb.vsup[k] * xc[i + 2];   // vsub[0] = vsup[nz-1] = 0
-                y[(size_t)k * g.plane + cl.c] = o1;
-                s1 += av[i] * o1;
-                if (yy) s2 += o1 * o1;
+            for (int i = 0; i < Zb; ++i) {
+                const int k = kb + i;
+                if (k < cl.k1) {
+                    const T c = xc[i + 1];
+                    const T o1 = (xe[i] - (T)2 * c + xw[i]) * g.idx2 + (xn[i] - (T)2 * c + xs[i]) * g.idy2 +
+                                 tb.vdiag[k] * c + tb.vsub[k] * xc[i] + tb.vsup[k] * xc[i + 2];   // vsub[0] = vsup[nz-1] = 0
+                    y[(size_t)k * g.plane + cl.c] = o1;
+                    s1 += av[i] * o1;
+                    if (yy) s2 += o1 * o1;
+                }
             }
         }
     }
@@ -391,10 +393,13 @@ __global__ void __launch_bounds__(kKryThreads) k_kry_apply(Grid<T> g, Tabs<T> tb
 // column, kLineBatch levels loaded before use; the forward sweep leaves its
 // values in out.
 template <typename T>
-__global__ void __launch_bounds__(kKryThreads) k_kry_line(Grid<T> g, Tabs<T> tb, const T* in, T* out,
-                                                          const KrySc* sc) {
+__global__ void __launch_bounds__(kKryThreads, 2) k_kry_line(Grid<T> g, Tabs<T> tb, const T* __restrict__ in,
+                                                          T* __restrict__ out, const KrySc* sc) {
     if (sc->done || sc->half) return;
     constexpr int B = kLineBatch<T>;
+    const T* __restrict__ vsub = tb.vsub;
+    const T* __restrict__ livd = tb.livd;
+    const T* __restrict__ lcp = tb.lcp;
     for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < g.plane; c += (size_t)gridDim.x * blockDim.x) {
         T dp = 0;
         for (int kb = 0; kb < g.nz; kb += B) {
@@ -405,7 +410,7 @@ __global__ void __launch_bounds__(kKryThreads) k_kry_line(Grid<T> g, Tabs<T> tb,
             for (int i = 0; i < B; ++i) {
                 const int k = kb + i;
                 if (k < g.nz) {
-                    dp = (b[i] - tb.vsub[k] * dp) * tb.livd[k];               // vsub[0] = 0
+                    dp = (b[i] - __ldg(&vsub[k]) * dp) * __ldg(&livd[k]);      // vsub[0] = 0
                     out[(size_t)k * g.plane + c] = dp;
                 }
             }
@@ -419,7 +424,7 @@ __global__ void __launch_bounds__(kKryThreads) k_kry_line(Grid<T> g, Tabs<T> tb,
             for (int i = 0; i < B; ++i) {
                 const int k = kb - i;
                 if (k >= 0) {
-                    xk = b[i] - tb.lcp[k] * xk;
+                    xk = b[i] - __ldg(&lcp[k]) * xk;
                     out[(size_t)k * g.plane + c] = xk;
                 }
             }
