@@ -85,14 +85,20 @@ def field_bytes(n, nz, elem=4):
     return elem * n * n * (3 * nz + 1)
 
 
-def make_fields(req: Request, dtype, device, generator):
+def make_fields(req: Request, dtype, device, generator, out=None):
     """Synthetic N(0,1) provisional velocities of a request, generated on the
-    device from the request's seed (w's bottom and top faces are zero)."""
+    device from the request's seed (w's bottom and top faces are zero), into
+    `out` = (u, v, w) when given."""
     generator.manual_seed(req.seed)
     n, nz = req.n, req.nz
-    u = torch.randn((nz, n, n), dtype=dtype, device=device, generator=generator)
-    v = torch.randn((nz, n, n), dtype=dtype, device=device, generator=generator)
-    w = torch.randn((nz + 1, n, n), dtype=dtype, device=device, generator=generator)
+    if out is None:
+        out = (torch.empty((nz, n, n), dtype=dtype, device=device),
+               torch.empty((nz, n, n), dtype=dtype, device=device),
+               torch.empty((nz + 1, n, n), dtype=dtype, device=device))
+    u, v, w = out
+    torch.randn((nz, n, n), dtype=dtype, device=device, generator=generator, out=u)
+    torch.randn((nz, n, n), dtype=dtype, device=device, generator=generator, out=v)
+    torch.randn((nz + 1, n, n), dtype=dtype, device=device, generator=generator, out=w)
     w[0].zero_()
     w[nz].zero_()
     return u, v, w
@@ -113,10 +119,32 @@ class ProjectionServer:
 
     def prewarm(self, sizes):
         """Build the plans of the given (n, nz) sizes so they are resident
-        before requests arrive.  Returns the set-up time [s]."""
+        before requests arrive; run one solve per horizontal size (the
+        kernels depend on n only), so that the CUDA runtime has loaded every
+        kernel the stream will use before the first arrival (it loads a
+        kernel on its first launch, a few ms each); and grow the allocator's
+        pool to the HBM budget once (request buffers are carved from it, so
+        the serving loop makes no device allocation).  Returns the set-up
+        time [s]."""
         t = time.perf_counter()
         for n, nz in sizes:
             self.plans.get(n, nz, self.precision)
+        smallest = {}
+        for n, nz in sizes:
+            smallest[n] = min(nz, smallest.get(n, nz))
+        for n, nz in sorted(smallest.items()):
+            plan = self.plans.get(n, nz, self.precision)
+            u = torch.zeros((nz, n, n), dtype=self.dtype, device=self.device)
+            v = torch.zeros_like(u)
+            w = torch.zeros((nz + 1, n, n), dtype=self.dtype, device=self.device)
+            ws = torch.empty(max(plan.workspace_bytes, 256), dtype=torch.uint8, device=self.device)
+            MP.monc_proj_solve(plan.handle, u, v, w, u, v, w, None, ws, torch.cuda.current_stream(self.device))
+            del u, v, w, ws
+        free, _ = torch.cuda.mem_get_info(self.device)
+        pool = int(min(self.hbm_budget, 0.8 * free))
+        if pool > 0:
+            block = torch.empty(pool, dtype=torch.uint8, device=self.device)
+            del block
         torch.cuda.synchronize(self.device)
         return time.perf_counter() - t
 
@@ -175,9 +203,16 @@ class ProjectionServer:
                 queue.popleft()
                 slot = free_slots.pop()
                 stream = self.streams[slot]
+                # buffers come from the current stream's pool (one pool for
+                # every slot, grown once by prewarm); record_stream below
+                # keeps a buffer from reuse until its slot's work is done
+                n, nz = req.n, req.nz
+                u = torch.empty((nz, n, n), dtype=self.dtype, device=self.device)
+                v = torch.empty((nz, n, n), dtype=self.dtype, device=self.device)
+                w = torch.empty((nz + 1, n, n), dtype=self.dtype, device=self.device)
+                ws = torch.empty(max(plan.workspace_bytes, 256), dtype=torch.uint8, device=self.device)
                 with torch.cuda.stream(stream):
-                    u, v, w = make_fields(req, self.dtype, self.device, self.generator)
-                    ws = torch.empty(max(plan.workspace_bytes, 256), dtype=torch.uint8, device=self.device)
+                    make_fields(req, self.dtype, self.device, self.generator, out=(u, v, w))
                     MP.monc_proj_solve(plan.handle, u, v, w, u, v, w, None, ws, stream)
                     ev = torch.cuda.Event(enable_timing=True)
                     ev.record(stream)
