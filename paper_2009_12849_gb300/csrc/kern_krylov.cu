@@ -516,8 +516,12 @@ __global__ void __launch_bounds__(kKryThreads) k_kry_level0(size_t plane, const 
     block_reduce(acc, 0.0, rd, blockIdx.x);
 }
 
-// u_out = u - G phi in FP64 from the iterate shifted by the pin; w zero on
-// the bottom and top faces.  (Stencil tiles.)
+// u_out = u - G phi with phi the iterate shifted by the pin; w zero on the
+// bottom and top faces.  (Stencil tiles.)  FP64 plans: in FP64.  FP32: the
+// differences of x = x_hi + x_lo are taken part by part, (x_hi' - x_hi) +
+// (x_lo' - x_lo); each part's difference of two floats is rounded once,
+// relative to the difference itself, so the gradient keeps FP32 accuracy
+// relative to G phi (not to phi) without FP64 arithmetic.
 template <typename T>
 __global__ void __launch_bounds__(kKryThreads) k_kry_correct(Grid<T> g, const T* xh, const T* xl, const T* u,
                                                              const T* v, const T* w, const double* idzn, T* uo, T* vo,
@@ -525,16 +529,34 @@ __global__ void __launch_bounds__(kKryThreads) k_kry_correct(Grid<T> g, const T*
     Col cl;
     if (!tile_column(g, cl)) return;
     const double m = sc->mean;
-    double xd = (cl.k0 > 0) ? x_at(xh, xl, (size_t)(cl.k0 - 1) * g.plane + cl.c) - m : 0.0;
-    for (int k = cl.k0; k < cl.k1; ++k) {
-        const size_t o = (size_t)k * g.plane;
-        const size_t q = o + cl.c;
-        const double c = x_at(xh, xl, q) - m;
-        uo[q] = (T)((double)u[q] - ((x_at(xh, xl, o + cl.ce) - m) - c) * g.idx64);
-        vo[q] = (T)((double)v[q] - ((x_at(xh, xl, o + cl.cn) - m) - c) * g.idy64);
-        wo[q] = (k > 0) ? (T)((double)w[q] - (c - xd) * idzn[k]) : (T)0;
-        if (phi) phi[q] = (T)c;
-        xd = c;
+    if constexpr (sizeof(T) == 8) {
+        double xd = (cl.k0 > 0) ? xh[(size_t)(cl.k0 - 1) * g.plane + cl.c] - m : 0.0;
+        for (int k = cl.k0; k < cl.k1; ++k) {
+            const size_t o = (size_t)k * g.plane;
+            const size_t q = o + cl.c;
+            const double c = xh[q] - m;
+            uo[q] = u[q] - ((xh[o + cl.ce] - m) - c) * g.idx64;
+            vo[q] = v[q] - ((xh[o + cl.cn] - m) - c) * g.idy64;
+            wo[q] = (k > 0) ? w[q] - (c - xd) * idzn[k] : 0.0;
+            if (phi) phi[q] = c;
+            xd = c;
+        }
+    } else {
+        const size_t qd = (size_t)(cl.k0 > 0 ? cl.k0 - 1 : 0) * g.plane + cl.c;
+        float hd = xh[qd], ld = xl[qd];
+        for (int k = cl.k0; k < cl.k1; ++k) {
+            const size_t o = (size_t)k * g.plane;
+            const size_t q = o + cl.c;
+            const float hc = xh[q], lc = xl[q];
+            const float gx = (xh[o + cl.ce] - hc) + (xl[o + cl.ce] - lc);
+            const float gy = (xh[o + cl.cn] - hc) + (xl[o + cl.cn] - lc);
+            uo[q] = u[q] - gx * g.idx;
+            vo[q] = v[q] - gy * g.idy;
+            wo[q] = (k > 0) ? w[q] - ((hc - hd) + (lc - ld)) * (float)idzn[k] : 0.f;
+            if (phi) phi[q] = (float)(((double)hc + (double)lc) - m);
+            hd = hc;
+            ld = lc;
+        }
     }
     if (cl.k1 == g.nz) wo[g.n + cl.c] = (T)0;
 }
