@@ -321,8 +321,9 @@ int monc_proj_autotune(monc_proj_plan_t plan, const void* u, const void* v, cons
  * MONC_PROJ_EBREAKDOWN when a BiCGStab denominator is exactly zero (in both
  * cases the outputs hold the projection with the last iterate); EINVAL for a
  * bad argument; ECUDA for a failed launch or copy.
- * The calling thread waits on `stream` once per iteration (the convergence
- * test reads the residual back), so the call cannot be captured into a graph.
+ * The calling thread waits on `stream` every 8 iterations (the convergence
+ * test reads the residual back; iterations enqueued past the one that stops
+ * do nothing), so the call cannot be captured into a graph.
  */
 typedef enum { MONC_PROJ_PC_NONE = 0, MONC_PROJ_PC_LINE = 1 } monc_proj_precond_t;
 int monc_proj_krylov_workspace_size(monc_proj_plan_t plan, size_t* bytes);

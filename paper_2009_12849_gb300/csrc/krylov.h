@@ -35,8 +35,8 @@ struct KrylovResult {
 
 size_t krylov_workspace_bytes(int nx, int ny, int nz, int nsm, bool fp32);
 
-// Runs the whole solve on `st`, reading the residual back once per
-// iteration (the calling thread waits on the stream).  Returns a cudaError_t.
+// Runs the whole solve on `st`, reading the residual back every few
+// iterations (the calling thread waits on the stream).  Returns a cudaError_t.
 cudaError_t krylov_run(const KrylovProblem& kp, cudaStream_t st, KrylovResult* res);
 
 }  // namespace mp
