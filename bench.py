@@ -244,6 +244,29 @@ def cpu_threads():
     return os.cpu_count() or 1
 
 
+# ------------------------------------------------------------------ replicas (N > 1)
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of the ranks' values: the slowest replica's time."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(seed: int, rank: int) -> int:
+    """Each rank projects its own replica of the workload (independent inputs)."""
+    return seed + 1000 * rank
+
+
+def job_throughput(world: int, npts: int, ms: float) -> float:
+    """Whole-job Mpts/s: the points all replicas projected over the slowest one's time."""
+    return world * npts / (ms * 1e-3) / 1e6
+
+
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args, rank, world):
@@ -298,7 +321,7 @@ def main():
     g, seed, mode = workload_grid()
     npts = g.nx * g.ny * g.nz
     # each rank projects its own replica of the workload (independent problems)
-    u_h, v_h, w_h = W.random_fields_f32(g, seed + 1000 * rank, mode)
+    u_h, v_h, w_h = W.random_fields_f32(g, replica_seed(seed, rank), mode)
     u = torch.from_numpy(u_h).to(dev)
     v = torch.from_numpy(v_h).to(dev)
     w = torch.from_numpy(w_h).to(dev)
@@ -330,12 +353,8 @@ def main():
     clk = clocks.stop()
     MP.monc_proj_profile(P.plan, False)
     prof = MP.monc_proj_profile_read(P.plan)
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * npts / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev)
+    value = job_throughput(world, npts, ms)
     status = P.sync_status()
 
     # ---- end to end through the C ABI with host buffers (monc_proj_solve_host):
@@ -374,11 +393,7 @@ def main():
         lanes[0][0].wait_stream(ln[0])
     e1.record(lanes[0][0])
     torch.cuda.synchronize(dev)
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world, dev)
     e2e_match = bool(torch.equal(lanes[0][1][0], out[0].cpu()))
     del lanes
     field_bytes = sum(x.numel() * x.element_size() for x in (uh, vh, wh))
@@ -505,7 +520,7 @@ def main():
                           "unit": "GB/s", "frac": path_gbs / peak},
         "phases_ms": {k: v / max(nsolves, 1) for k, v in phases.items()},
         "cpu_baseline": cpu,
-        "e2e": {"value": world * npts / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
+        "e2e": {"value": job_throughput(world, npts, e2e_ms), "unit": UNIT,
                 "h2d_bytes_per_step": field_bytes, "d2h_bytes_per_step": field_bytes,
                 "ms_per_step": e2e_ms, "api": f"monc_proj_solve_host, {nl} streams",
                 "matches_device_solve": e2e_match},
