@@ -60,3 +60,32 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert L.monc_proj_plan(None, 8, 8, 4, 1.0, 1.0, None, None, None, 0, None) == lib.MONC_PROJ_EINVAL
     assert L.monc_proj_workspace_size(None, None) == lib.MONC_PROJ_EINVAL
     assert L.monc_proj_destroy(None) == lib.MONC_PROJ_OK
+
+
+def test_krylov_entry_points_reject_bad_arguments_without_gpu(lib):
+    L = lib.load_library()
+    assert L.monc_proj_krylov_workspace_size(None, None) == lib.MONC_PROJ_EINVAL
+    assert L.monc_proj_solve_krylov(None, None, None, None, None, None, None, None, None, 1e-4, 10, 1,
+                                    None, None, None) == lib.MONC_PROJ_EINVAL
+    assert "iteration limit" in lib.monc_proj_status_string(lib.MONC_PROJ_ENOCONV)
+    assert "broke down" in lib.monc_proj_status_string(lib.MONC_PROJ_EBREAKDOWN)
+
+
+def test_plan_validation_without_gpu(lib):
+    import ctypes
+    L = lib.load_library()
+    h = ctypes.c_void_p()
+    nz = 4
+    dz = (ctypes.c_double * nz)(*([25.0] * nz))
+    rc = (ctypes.c_double * nz)(*([1.0] * nz))
+    rf = (ctypes.c_double * (nz + 1))(*([1.0] * (nz + 1)))
+    # 7 and 14 are not of the form 2^a 3^b 5^c
+    assert L.monc_proj_plan(ctypes.byref(h), 7, 8, nz, 10.0, 10.0, dz, rc, rf, 1, None) == lib.MONC_PROJ_EUNSUPPORTED
+    assert L.monc_proj_plan(ctypes.byref(h), 8, 14, nz, 10.0, 10.0, dz, rc, rf, 1, None) == lib.MONC_PROJ_EUNSUPPORTED
+    # non-positive or non-finite spacings, an unknown precision
+    assert L.monc_proj_plan(ctypes.byref(h), 8, 8, nz, 0.0, 10.0, dz, rc, rf, 1, None) == lib.MONC_PROJ_EINVAL
+    assert L.monc_proj_plan(ctypes.byref(h), 8, 8, nz, 10.0, float("nan"), dz, rc, rf, 1, None) == lib.MONC_PROJ_EINVAL
+    bad = (ctypes.c_double * nz)(*([25.0, -1.0, 25.0, 25.0]))
+    assert L.monc_proj_plan(ctypes.byref(h), 8, 8, nz, 10.0, 10.0, bad, rc, rf, 1, None) == lib.MONC_PROJ_EINVAL
+    assert L.monc_proj_plan(ctypes.byref(h), 8, 8, nz, 10.0, 10.0, dz, rc, rf, 7, None) == lib.MONC_PROJ_EINVAL
+    assert h.value is None
