@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batch measurement")
     ap.add_argument("--no-refined", action="store_true", help="skip the refinement (mixed passes on FP64 fields) leg")
     ap.add_argument("--no-krylov", action="store_true", help="skip the BiCGStab pressure-solver leg")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 64^3 and 256^2 x 128 legs (the other configurations of the workload set)")
     ap.add_argument("--e2e-lanes", type=int, default=4,
                     help="streams (each with its own staging area and workspace) taking turns in the e2e leg")
     ap.add_argument("--serve-requests", type=int, default=10000,
@@ -167,14 +169,33 @@ def phase_bytes(g, phase: str, elem: int) -> float:
         "inv_rows": 3 * spec + 2 * fields_in,           # 3 spectra + u,v,w -> u,v,w
         "fwd_fused": fields_in + spec,                  # u,v,w -> D^ (x-spectra stay in L2)
         "inv_fused": 2 * spec + 2 * fields_in,          # p^, gz^, u,v,w -> u,v,w
+        "fwd_pipe": fields_in + spec,                   # u,v,w -> D^ (x-spectra handed off in L2)
+        "inv_pipe": 2 * spec + 2 * fields_in,           # p^, gz^, u,v,w -> u,v,w (channel spectra in L2)
     }[phase]
 
 
 def path_bytes_per_point(elem: int) -> float:
-    """Algorithmic bytes per grid point of the whole projection: read u,v,w (3),
-    write D^ (1/2 complex per point = 1 real), read D^, write p^ and gz^, read
-    them, read u,v,w again, write u,v,w: 15 reals per point."""
-    return 15.0 * elem
+    """Algorithmic bytes per grid point of the whole projection: read u,v,w (3
+    reals), write D^ (a half spectrum: 1 real per point), read D^, write p^,
+    read p^, read u,v,w again, write u,v,w -- 13 reals per point (52 B in
+    FP32).  The spectral w-gradient the mixed path also writes and reads is
+    not counted, nor any hand-off between the passes of a 2D transform."""
+    return 13.0 * elem
+
+
+def recorded_path_traffic():
+    """DRAM bytes of one whole step (all five kernels) from the committed ncu
+    summary, or None if the kernels changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None
+    if rec.get("csrc_hash") != csrc_hash() or rec.get("workload") != WORKLOAD:
+        return None
+    ks = rec.get("kernels", {})
+    vals = [k.get("dram_bytes_per_launch") for k in ks.values()]
+    return None if not vals or any(v is None for v in vals) else float(sum(vals))
 
 
 # Sources of the BiCGStab solver: no kernel of the FFT path includes them, so
@@ -421,6 +442,38 @@ def main():
             fp64["accuracy"] = verify(g, (u64, v64, w64), o64)
         P64.close()
 
+    # ---- the vertical solve with FP64 elimination on every column (FP32
+    # storage): the reading of a3 in which no column runs FP32 arithmetic
+    a3_variants = {"fp32_fp64_split": {"ms_per_step": ms, "value": value, "unit": UNIT,
+                                       "fp64_columns": P.info().get("fp64_columns"),
+                                       "columns": P.info().get("total_columns")}}
+    if not args.no_fp64:
+        PZ = MP.Projector.from_grid(g, "mixed_z64", dev)
+        oz = (torch.empty_like(u), torch.empty_like(v), torch.empty_like(w))
+        for _ in range(2):
+            PZ.solve(u, v, w, out=oz)
+        torch.cuda.synchronize(dev)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        nzr = 5
+        MP.monc_proj_profile(PZ.plan, True)
+        a0.record(stream)
+        for _ in range(nzr):
+            PZ.solve(u, v, w, out=oz)
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        MP.monc_proj_profile(PZ.plan, False)
+        pz = MP.monc_proj_profile_read(PZ.plan)
+        msz = a0.elapsed_time(a1) / nzr
+        leg = {"ms_per_step": msz, "value": npts / (msz * 1e-3) / 1e6, "unit": UNIT,
+               "tridiag_ms": pz["phases"].get("tridiag", 0.0) / max(pz["solves"], 1),
+               "fp64_columns": PZ.info().get("fp64_columns")}
+        if not args.no_check and rank == 0:
+            leg["accuracy"] = verify(g, (u, v, w), oz, o64)
+        a3_variants["fp64_all_columns"] = leg
+        PZ.close()
+        del oz
+
     # ---- refinement: mixed passes on FP64 fields (FP64-level accuracy)
     refined = None
     if not args.no_fp64 and not args.no_refined:
@@ -458,27 +511,27 @@ def main():
     # ---- uneven batch of 64 projections (one batched call, and its CUDA-graph replay)
     batch = None
     if not args.no_batch and rank == 0:
-        batch = measure_batch(dev, stream)
+        batch = measure_batch(dev, stream, check=not args.no_check)
 
     # ---- serving: Poisson arrivals, continuous batching, HBM admission
     serving = None
     if args.serve_requests > 0 and rank == 0:
-        from paper_2009_12849_gb300 import serve as S
-        srv = S.ProjectionServer(dev, hbm_budget=40e9, slots=32)
-        # warm-up stream (another seed of the recipe): the first serving pass
-        # of a process runs with a p99 about three times the steady state's
-        srv.run(S.requests_from_recipe(min(1000, args.serve_requests), 2000.0, 5))
-        reqs = S.requests_from_recipe(args.serve_requests, 2000.0, 4)
-        serving = srv.run(reqs)
-        serving["warmup_requests"] = min(1000, args.serve_requests)
-        serving.update({"rate_per_s": 2000.0, "recipe": "sizes 128-512 log-uniform (nearest 2^a3^b5^c) "
-                                                       "x nz 64-192, seed 4, mixed precision"})
-        srv.close()
+        serving = measure_serving(dev, args.serve_requests, args.no_check)
 
     # ---- BiCGStab pressure solver to the paper's stopping criterion
     krylov = None
     if not args.no_krylov and rank == 0:
         krylov = measure_krylov(dev, stream, args.no_check)
+
+    # ---- the other configurations: 64^3 and 256^2 x 128 (FP64 workloads; the
+    # mixed path timed beside them)
+    configs = None
+    if not args.no_configs and rank == 0:
+        configs = measure_configs(dev, stream, args.no_check)
+
+    # ---- the host link the e2e leg runs over: plain page-locked copies of the
+    # step's bytes, each direction alone and both at once
+    link = measure_link(dev, field_bytes) if rank == 0 else None
 
     if rank != 0:
         if world > 1:
@@ -496,6 +549,7 @@ def main():
     traffic = recorded_traffic(dom)
     path_bpp = path_bytes_per_point(4)
     path_gbs = path_bpp * npts / (ms * 1e-3) / 1e9
+    path_traffic = recorded_path_traffic()
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -513,11 +567,12 @@ def main():
                    "dz": "geometric 5->50 m", "precision": "mixed", "seed": seed,
                    "l2": "inputs larger than L2 (1.07 GB per field), no flush",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "algorithmic_bytes": dom_bytes, "ms_per_launch": dom_ms},
-        "path_roofline": {"bytes_per_point": path_bpp, "achieved": path_gbs, "peak": peak,
-                          "unit": "GB/s", "frac": path_gbs / peak},
+        "roofline": {"bound": "hbm", "scope": "whole projection step (all kernels)",
+                     "bytes_per_point": path_bpp, "achieved": path_gbs, "peak": peak, "peak_kind": peak_kind,
+                     "unit": "GB/s", "frac": path_gbs / peak, "traffic": path_traffic,
+                     "algorithmic_bytes": path_bpp * npts,
+                     "kernel": {"name": dom, "achieved": achieved, "frac": achieved / peak, "traffic": traffic,
+                                "algorithmic_bytes": dom_bytes, "ms_per_launch": dom_ms}},
         "phases_ms": {k: v / max(nsolves, 1) for k, v in phases.items()},
         "cpu_baseline": cpu,
         "e2e": {"value": job_throughput(world, npts, e2e_ms), "unit": UNIT,
@@ -527,7 +582,10 @@ def main():
         "clocks": clk,
         "gpu_launches": nsolves * len(phases),
         "fp64_path": fp64,
+        "a3_variants": a3_variants,
         "refined_path": refined,
+        "configs": configs,
+        "link": link,
         "krylov_path": krylov,
         "batch": batch,
         "serving": serving,
@@ -539,7 +597,7 @@ def main():
         dist.destroy_process_group()
 
 
-def measure_batch(dev, stream, count=64, reps=5):
+def measure_batch(dev, stream, count=64, reps=5, check=True):
     """64 uneven projections (n from {64,96,128,192,256}, nz from
     {64,96,128,160}, mixed precision, seed 3): time of one batched call and of
     a CUDA-graph replay of it."""
@@ -587,10 +645,146 @@ def measure_batch(dev, stream, count=64, reps=5):
     ms, ms_graph = timed()
     B.close()
     tuned = sorted({tuple(x) for x in shapes})
-    return {"instances": count, "points": pts, "ms_per_batch": ms, "mpts_per_s": pts / (ms * 1e-3) / 1e6,
-            "graph_ms_per_batch": ms_graph, "graph_mpts_per_s": pts / (ms_graph * 1e-3) / 1e6,
-            "autotuned": True, "shapes_kept": [list(x) for x in tuned],
-            "default_shapes": {"ms_per_batch": ms0, "graph_ms_per_batch": ms_graph0}}
+    res = {"instances": count, "points": pts, "ms_per_batch": ms, "mpts_per_s": pts / (ms * 1e-3) / 1e6,
+           "graph_ms_per_batch": ms_graph, "graph_mpts_per_s": pts / (ms_graph * 1e-3) / 1e6,
+           "autotuned": True, "shapes_kept": [list(x) for x in tuned],
+           "default_shapes": {"ms_per_batch": ms0, "graph_ms_per_batch": ms_graph0}}
+    if check:
+        # every instance against its own FP64 GPU solve (the path the parity
+        # tests pin to the FP64 oracle) and its divergence residual
+        errs, divs = [], []
+        for g, a in zip(grids, args):
+            P64 = MP.Projector.from_grid(g, "fp64", dev)
+            ref = P64.solve(*(t.double() for t in a[:3]))
+            acc = verify(g, a[:3], a[3:6], ref)
+            errs.append(acc["rel_err_vs_fp64_path"])
+            divs.append(acc["div_residual"])
+            P64.close()
+        res["accuracy"] = {"max_rel_err_vs_fp64_path": max(errs), "max_div_residual": max(divs),
+                           "instances": len(errs)}
+    return res
+
+
+def measure_serving(dev, nreq, no_check, samples=20):
+    """The serving recipe: plans for the whole size envelope built first
+    (every 2^a3^b5^c n in [128, 512] x nz in [64, 192], chosen without the
+    request list), then the process's first serving pass (2000 requests of
+    another seed: the cold p50/p99) and the measured pass (nreq requests, seed
+    4), with every (nreq // samples)-th output kept and checked."""
+    import torch
+    from paper_2009_12849_gb300 import monc_proj as MP
+    from paper_2009_12849_gb300 import serve as S
+    from paper_2009_12849_gb300 import workloads as W
+    srv = S.ProjectionServer(dev, hbm_budget=40e9, slots=32)
+    setup = srv.prewarm_envelope()
+    cold = srv.run(sorted(S.requests_from_recipe(min(2000, nreq), 2000.0, 5), key=lambda r: r.t))
+    reqs = sorted(S.requests_from_recipe(nreq, 2000.0, 4), key=lambda r: r.t)
+    every = max(1, nreq // samples)
+    stats = srv.run(reqs, keep_outputs=not no_check, keep_every=every)
+    outputs = stats.pop("outputs", None)
+    stats.update({"rate_per_s": 2000.0, "prewarm_s": setup,
+                  "recipe": "sizes 128-512 log-uniform (nearest 2^a3^b5^c) x nz 64-192, seed 4, mixed precision",
+                  "prewarm": "every 2^a3^b5^c n in [128, 512] x nz in [64, 192], built before any request",
+                  "cold": {k: cold[k] for k in ("requests", "served", "p50_ms", "p99_ms", "max_ms", "mean_ms",
+                                                "mpts_per_s")}})
+    if outputs is not None:
+        gen = torch.Generator(device=dev)
+        errs, divs, sizes = [], [], []
+        for i, o in enumerate(outputs):
+            if o is None:
+                continue
+            r = reqs[i]
+            g = W.serving_grid(r.n, r.nz)
+            ins = S.make_fields(r, torch.float32, dev, gen)
+            P64 = MP.Projector.from_grid(g, "fp64", dev)
+            ref = P64.solve(*(t.double() for t in ins))
+            acc = verify(g, ins, o, ref)
+            errs.append(acc["rel_err_vs_fp64_path"])
+            divs.append(acc["div_residual"])
+            sizes.append([r.n, r.n, r.nz])
+            P64.close()
+        stats["accuracy"] = {"max_rel_err_vs_fp64_path": max(errs), "max_div_residual": max(divs),
+                             "requests_checked": len(errs), "sizes": sizes}
+    srv.close()
+    return stats
+
+
+def measure_configs(dev, stream, no_check, reps=30):
+    """The 64^3 (seed 0) and 256^2 x 128 (seed 1, with the large-scale mode)
+    workloads, FP64 as specified and mixed beside them; accuracy of the mixed
+    path against the FP64 path and the divergence residual of both."""
+    import torch
+    from paper_2009_12849_gb300 import monc_proj as MP
+    from paper_2009_12849_gb300 import workloads as W
+    out = {}
+    for name, (g, seed, mode) in (("proj64_fp64", W.workload_64cube()), ("proj256x128_fp64", W.workload_256())):
+        npts = g.nx * g.ny * g.nz
+        host = W.random_fields(g, seed, mode)
+        leg = {"nx": g.nx, "ny": g.ny, "nz": g.nz, "points": npts}
+        ref = None
+        for prec in ("fp64", "mixed"):
+            P = MP.Projector.from_grid(g, prec, dev)
+            u, v, w = (torch.tensor(a, dtype=P.dtype, device=dev) for a in host)
+            o = (torch.empty_like(u), torch.empty_like(v), torch.empty_like(w))
+            for _ in range(3):
+                P.solve(u, v, w, out=o)
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                P.solve(u, v, w, out=o)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            msr = e0.elapsed_time(e1) / reps
+            r = {"ms_per_step": msr, "value": npts / (msr * 1e-3) / 1e6, "unit": UNIT,
+                 "device_status": P.sync_status()}
+            if not no_check:
+                r["accuracy"] = verify(g, (u, v, w), o, ref)
+            if prec == "fp64":
+                ref = tuple(t.clone() for t in o)
+            leg[prec] = r
+            P.close()
+        out[name] = leg
+    return out
+
+
+def measure_link(dev, total_bytes, chunk=1 << 30):
+    """Page-locked host <-> device copy rates (GB/s) over up to 1 GiB: each
+    direction alone, then both at once on two streams (the pattern of the e2e
+    leg, whose copies in and out of different steps overlap)."""
+    import torch
+    n = int(min(total_bytes, chunk))
+    h_in = torch.empty(n, dtype=torch.uint8).pin_memory()
+    h_out = torch.empty(n, dtype=torch.uint8).pin_memory()
+    d_in = torch.empty(n, dtype=torch.uint8, device=dev)
+    d_out = torch.empty(n, dtype=torch.uint8, device=dev)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def timed(h2d, d2h, reps=3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(s1)
+        s2.wait_event(e0)
+        for _ in range(reps):
+            if h2d:
+                with torch.cuda.stream(s1):
+                    d_in.copy_(h_in, non_blocking=True)
+            if d2h:
+                with torch.cuda.stream(s2):
+                    h_out.copy_(d_out, non_blocking=True)
+        s1.wait_stream(s2)
+        e1.record(s1)
+        torch.cuda.synchronize(dev)
+        return reps * n * (int(h2d) + int(d2h)) / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+    for _ in range(2):
+        timed(True, True, 1)
+    res = {"bytes_per_copy": n, "h2d_gbs": timed(True, False), "d2h_gbs": timed(False, True),
+           "both_directions_gbs": timed(True, True)}
+    del h_in, h_out, d_in, d_out
+    return res
 
 
 def _divergence(g, u, v, w, k0, k1):

@@ -40,7 +40,11 @@
  * variable MONC_PROJ_REFINE_PASSES, 1..4, read when a plan is made, sets the
  * count).  The workspace also holds one FP64 field.  This is the
  * single-precision solve with a double-precision restart that the paper
- * proposes as further work (§5).
+ * proposes as further work (§5).  MONC_PROJ_MIXED_Z64: as MONC_PROJ_MIXED,
+ * but the vertical elimination runs in FP64 arithmetic for every column (the
+ * FP32 storage of the spectra is unchanged); slower on this GPU, whose FP64
+ * rate is a small fraction of its FP32 rate.  Plans of it report it as
+ * their precision; everything else about them is that of MONC_PROJ_MIXED.
  *
  * Errors.  Every call returns a monc_proj_status.  Nothing aborts, traps or
  * throws across this boundary.  Problems found on the device (a bounded
@@ -78,11 +82,36 @@ typedef enum {
 typedef enum {
     MONC_PROJ_FP64 = 0,
     MONC_PROJ_MIXED = 1,
-    MONC_PROJ_REFINED = 2
+    MONC_PROJ_REFINED = 2,
+    MONC_PROJ_MIXED_Z64 = 3
 } monc_proj_precision;
 
 /* Largest nx or ny a plan accepts. */
 #define MONC_PROJ_MAX_N 4096
+
+/*
+ * Allocator of plan tables (the paper has no counterpart).
+ *
+ * By default monc_proj_plan takes its device tables (a few tens of KB to a
+ * few MB per plan) from cudaMalloc and monc_proj_destroy returns them with
+ * cudaFree.  A host application that manages device memory through its own
+ * pool installs its allocator here instead:
+ *
+ *   alloc(bytes, user)    returns device memory of at least `bytes` on the
+ *                         current device, 256-byte aligned, or NULL on failure
+ *   release(ptr, user)    returns memory obtained from alloc
+ *   user                  passed back unchanged to both
+ *
+ * Both NULL restore cudaMalloc / cudaFree; exactly one NULL is EINVAL.  The
+ * setting is process-wide and applies to plans created afterwards; a plan
+ * keeps the release function it was created with.  When alloc returns NULL,
+ * monc_proj_plan returns MONC_PROJ_ENOMEM before it touches the device.
+ * Set it before plans are created concurrently from other threads.
+ * Workspaces and fields are always the caller's.
+ */
+typedef void* (*monc_proj_alloc_fn)(size_t bytes, void* user);
+typedef void (*monc_proj_free_fn)(void* ptr, void* user);
+int monc_proj_set_allocator(monc_proj_alloc_fn alloc, monc_proj_free_fn release, void* user);
 
 /*
  * Build a plan for one grid (the set-up of steps a2-a4: twiddle tables,
@@ -96,12 +125,20 @@ typedef enum {
  *   dz         host array [nz], layer thicknesses [m], > 0
  *   rho_c      host array [nz], reference density at cell centres, > 0
  *   rho_f      host array [nz+1], reference density at w faces, > 0
- *   precision  MONC_PROJ_FP64, MONC_PROJ_MIXED or MONC_PROJ_REFINED
+ *   precision  MONC_PROJ_FP64, MONC_PROJ_MIXED, MONC_PROJ_REFINED or
+ *              MONC_PROJ_MIXED_Z64
  *   stream     cudaStream_t (may be NULL) used for the plan's uploads; the
  *              call returns after they have completed
  *
  * The host arrays are copied; the caller may free them when this returns.
  * The plan's device tables live on the device that is current at the call.
+ *
+ * Returns MONC_PROJ_ENOMEM when the tables cannot be allocated (see
+ * monc_proj_set_allocator).  The bounded dependency waits of the opt-in
+ * persistent kernels give up after a fixed number of polls (about a second)
+ * and latch a timeout that monc_proj_sync_status reports as
+ * MONC_PROJ_ETIMEOUT; MONC_PROJ_SPIN_LIMIT in the environment, read here,
+ * sets that number (0: give up at the first unmet poll, for tests).
  */
 int monc_proj_plan(monc_proj_plan_t* out, int nx, int ny, int nz, double dx, double dy,
                    const double* dz, const double* rho_c, const double* rho_f,
@@ -234,22 +271,26 @@ const char* monc_proj_phase_name(int phase);
  *
  * Arguments are those of monc_proj_plan followed by those of monc_proj_solve
  * (same layouts, types, alignment and in-place rules); there is no plan and
- * no workspace argument.  The call is asynchronous on `stream`.
+ * no workspace argument.  The work is enqueued on `stream`.
  *
  * Limits and behaviour:
  *  - a grid whose tables plus workspace exceed MONC_PROJ_NOALLOC_SCRATCH_BYTES
  *    is rejected with MONC_PROJ_ESCRATCH before anything is enqueued (about
  *    64 x 64 x 64 in FP64 or 80 x 80 x 64 in mixed precision fit);
- *  - the first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress, once per device, with that device current); make
- *    that first call before any stream capture begins;
+ *  - every call looks up the array's device address on the current device
+ *    (cudaGetSymbolAddress), so nothing is cached across calls or contexts;
+ *  - the tables are uploaded at every call with cudaMemcpyAsync from pageable
+ *    host memory that the call owns only while it runs, so the call may wait
+ *    for the work already on `stream` before it returns, and a call on a
+ *    stream that is being captured into a CUDA graph is refused with
+ *    MONC_PROJ_EUNSUPPORTED before anything is enqueued (a replay would read
+ *    host memory that no longer exists);
  *  - every call on a device shares the one array and overwrites the previous
  *    call's tables and workspace: calls whose GPU work overlaps (different
  *    streams, or different host threads without ordering) race and give wrong
  *    results.  Calls on one stream are ordered and safe;
- *  - the tables are uploaded from pageable host memory on `stream` at every
- *    call; device-detected errors of the call are not reported (there is no
- *    plan to latch them in).
+ *  - device-detected errors of the call are not reported (there is no plan
+ *    to latch them in).
  */
 #define MONC_PROJ_NOALLOC_SCRATCH_BYTES (32u << 20)
 int monc_proj_solve_noalloc(int nx, int ny, int nz, double dx, double dy,

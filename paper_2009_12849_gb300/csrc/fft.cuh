@@ -196,6 +196,22 @@ __device__ cplx<R>* fft_batch(cplx<R>* a, cplx<R>* b, int nb, int bstride,
     return a;
 }
 
+// Thread scope of a compile-time transform: the whole block (threads of the
+// block cooperate on its transforms and synchronise with __syncthreads), or
+// one warp (a warp transforms its own sequences in its own shared-memory
+// slice and synchronises with __syncwarp; the persistent pipeline kernels run
+// row transforms this way, eight independent warps to a block).
+struct BlockScope {
+    static __device__ __forceinline__ int tid() { return threadIdx.x; }
+    static __device__ __forceinline__ int size() { return blockDim.x; }
+    static __device__ __forceinline__ void sync() { __syncthreads(); }
+};
+struct WarpScope {
+    static __device__ __forceinline__ int tid() { return threadIdx.x & 31; }
+    static __device__ __forceinline__ int size() { return 32; }
+    static __device__ __forceinline__ void sync() { __syncwarp(); }
+};
+
 // ---------------------------------------------------------------------------
 // Compile-time plans for the common lengths.  Every stage's radix, Ns, n/R
 // and twiddle stride are constants; every thread holds at most E elements of
@@ -277,7 +293,7 @@ template <typename R, int N, int NS> struct StageIndex {
     static constexpr int value = stage_index_impl<R, N>(NS);
 };
 
-template <typename R, int N, int NS, int S>
+template <typename R, int N, int NS, int S, class Sc = BlockScope>
 __device__ __forceinline__ void ct_stage(cplx<R>* buf, int nb, int bstride, const cplx<R>* __restrict__ tws) {
     const cplx<R>* __restrict__ tw = tws + StageIndex<R, N, NS>::value * N;
     constexpr int RAD = StageRadix<R, N, NS>::value;
@@ -288,7 +304,7 @@ __device__ __forceinline__ void ct_stage(cplx<R>* buf, int nb, int bstride, cons
     cplx<R> x[NB][RAD];
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-        const int t = threadIdx.x + i * blockDim.x;
+        const int t = Sc::tid() + i * Sc::size();
         if (t < total) {
             const int b = t / NQ;
             const int q = t - b * NQ;
@@ -297,10 +313,10 @@ __device__ __forceinline__ void ct_stage(cplx<R>* buf, int nb, int bstride, cons
             for (int r = 0; r < RAD; ++r) x[i][r] = src[spad(q + r * NQ)];
         }
     }
-    __syncthreads();
+    Sc::sync();
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-        const int t = threadIdx.x + i * blockDim.x;
+        const int t = Sc::tid() + i * Sc::size();
         if (t < total) {
             const int b = t / NQ;
             const int q = t - b * NQ;
@@ -320,16 +336,16 @@ __device__ __forceinline__ void ct_stage(cplx<R>* buf, int nb, int bstride, cons
             for (int r = 0; r < RAD; ++r) dst[spad(base + r * NS)] = x[i][r];
         }
     }
-    __syncthreads();
+    Sc::sync();
 }
 
-template <typename R, int N, int NS, int S> struct CtFFT {
+template <typename R, int N, int NS, int S, class Sc = BlockScope> struct CtFFT {
     static __device__ __forceinline__ void run(cplx<R>* buf, int nb, int bstride, const cplx<R>* tw) {
-        ct_stage<R, N, NS, S>(buf, nb, bstride, tw);
-        CtFFT<R, N, NS * StageRadix<R, N, NS>::value, S>::run(buf, nb, bstride, tw);
+        ct_stage<R, N, NS, S, Sc>(buf, nb, bstride, tw);
+        CtFFT<R, N, NS * StageRadix<R, N, NS>::value, S, Sc>::run(buf, nb, bstride, tw);
     }
 };
-template <typename R, int N, int S> struct CtFFT<R, N, N, S> {
+template <typename R, int N, int S, class Sc> struct CtFFT<R, N, N, S, Sc> {
     static __device__ __forceinline__ void run(cplx<R>*, int, int, const cplx<R>*) {}
 };
 
@@ -374,7 +390,7 @@ __device__ __forceinline__ void bfly_map(int t, int nb, int& b, int& q) {
 
 // SYNC_IN: the inputs are read from the same shared buffer the stage writes,
 // so the block synchronises between the reads and the writes.
-template <typename R, int N, int S, bool BFAST, bool SYNC_IN = false, class Load>
+template <typename R, int N, int S, bool BFAST, bool SYNC_IN = false, class Sc = BlockScope, class Load>
 __device__ __forceinline__ void ct_first(cplx<R>* buf, int nb, int bstride, Load&& load) {
     using SI = StageInfo<R, N, 1>;
     constexpr int RAD = SI::RAD, NQ = SI::NQ;
@@ -384,7 +400,7 @@ __device__ __forceinline__ void ct_first(cplx<R>* buf, int nb, int bstride, Load
     cplx<R> x[NB][RAD];
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-        const int t = threadIdx.x + i * blockDim.x;
+        const int t = Sc::tid() + i * Sc::size();
         if (t < total) {
             int b, q;
             bfly_map<BFAST, NQ>(t, nb, b, q);
@@ -392,10 +408,10 @@ __device__ __forceinline__ void ct_first(cplx<R>* buf, int nb, int bstride, Load
             for (int r = 0; r < RAD; ++r) x[i][r] = load(b, q + r * NQ);
         }
     }
-    if (SYNC_IN) __syncthreads();
+    if (SYNC_IN) Sc::sync();
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-        const int t = threadIdx.x + i * blockDim.x;
+        const int t = Sc::tid() + i * Sc::size();
         if (t < total) {
             int b, q;
             bfly_map<BFAST, NQ>(t, nb, b, q);
@@ -405,20 +421,21 @@ __device__ __forceinline__ void ct_first(cplx<R>* buf, int nb, int bstride, Load
             for (int r = 0; r < RAD; ++r) dst[spad(q * RAD + r)] = x[i][r];
         }
     }
-    __syncthreads();
+    Sc::sync();
 }
 
-template <typename R, int N, int NS, int S, bool STOP = StageInfo<R, N, NS>::LAST> struct CtMid {
+template <typename R, int N, int NS, int S, class Sc = BlockScope, bool STOP = StageInfo<R, N, NS>::LAST>
+struct CtMid {
     static __device__ __forceinline__ void run(cplx<R>* buf, int nb, int bstride, const cplx<R>* tw) {
-        ct_stage<R, N, NS, S>(buf, nb, bstride, tw);
-        CtMid<R, N, StageInfo<R, N, NS>::NEXT, S>::run(buf, nb, bstride, tw);
+        ct_stage<R, N, NS, S, Sc>(buf, nb, bstride, tw);
+        CtMid<R, N, StageInfo<R, N, NS>::NEXT, S, Sc>::run(buf, nb, bstride, tw);
     }
 };
-template <typename R, int N, int NS, int S> struct CtMid<R, N, NS, S, true> {
+template <typename R, int N, int NS, int S, class Sc> struct CtMid<R, N, NS, S, Sc, true> {
     static __device__ __forceinline__ void run(cplx<R>*, int, int, const cplx<R>*) {}
 };
 
-template <typename R, int N, int S, bool BFAST, class Store>
+template <typename R, int N, int S, bool BFAST, class Sc = BlockScope, class Store>
 __device__ __forceinline__ void ct_last(const cplx<R>* buf, int nb, int bstride, const cplx<R>* __restrict__ tws,
                                         Store&& store) {
     constexpr int NS = LastNs<R, N>::value;
@@ -431,7 +448,7 @@ __device__ __forceinline__ void ct_last(const cplx<R>* buf, int nb, int bstride,
     const int total = NQ * nb;
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-        const int t = threadIdx.x + i * blockDim.x;
+        const int t = Sc::tid() + i * Sc::size();
         if (t < total) {
             int b, q;
             bfly_map<BFAST, NQ>(t, nb, b, q);
@@ -457,7 +474,7 @@ __device__ __forceinline__ void ct_last(const cplx<R>* buf, int nb, int bstride,
 // of the thread before any butterfly is transformed, so loads it issues (the
 // operands of the store's read-modify-write) are all in flight at once
 // instead of one butterfly at a time; then store(b, q, x, NS, i) as ct_last.
-template <typename R, int N, int S, bool BFAST, class Pre, class Store>
+template <typename R, int N, int S, bool BFAST, class Sc = BlockScope, class Pre, class Store>
 __device__ __forceinline__ void ct_last_pre(const cplx<R>* buf, int nb, int bstride, const cplx<R>* __restrict__ tws,
                                             Pre&& pre, Store&& store) {
     constexpr int NS = LastNs<R, N>::value;
@@ -470,7 +487,7 @@ __device__ __forceinline__ void ct_last_pre(const cplx<R>* buf, int nb, int bstr
     const int total = NQ * nb;
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-        const int t = threadIdx.x + i * blockDim.x;
+        const int t = Sc::tid() + i * Sc::size();
         if (t < total) {
             int b, q;
             bfly_map<BFAST, NQ>(t, nb, b, q);
@@ -479,7 +496,7 @@ __device__ __forceinline__ void ct_last_pre(const cplx<R>* buf, int nb, int bstr
     }
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-        const int t = threadIdx.x + i * blockDim.x;
+        const int t = Sc::tid() + i * Sc::size();
         if (t < total) {
             int b, q;
             bfly_map<BFAST, NQ>(t, nb, b, q);
@@ -503,7 +520,7 @@ __device__ __forceinline__ void ct_last_pre(const cplx<R>* buf, int nb, int bstr
 // Last stage for an output buffer that aliases the input: every thread
 // computes its butterflies into registers, the block synchronises, then the
 // results go to store(b, q, x, NS).
-template <typename R, int N, int S, bool BFAST, class Store>
+template <typename R, int N, int S, bool BFAST, class Sc = BlockScope, class Store>
 __device__ __forceinline__ void ct_last_sync(const cplx<R>* buf, int nb, int bstride, const cplx<R>* __restrict__ tws,
                                              Store&& store) {
     constexpr int NS = LastNs<R, N>::value;
@@ -517,7 +534,7 @@ __device__ __forceinline__ void ct_last_sync(const cplx<R>* buf, int nb, int bst
     cplx<R> x[NB][RAD];
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-        const int t = threadIdx.x + i * blockDim.x;
+        const int t = Sc::tid() + i * Sc::size();
         if (t < total) {
             int b, q;
             bfly_map<BFAST, NQ>(t, nb, b, q);
@@ -534,10 +551,10 @@ __device__ __forceinline__ void ct_last_sync(const cplx<R>* buf, int nb, int bst
             RegFFT<R, RAD, S>::run(x[i]);
         }
     }
-    __syncthreads();
+    Sc::sync();
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-        const int t = threadIdx.x + i * blockDim.x;
+        const int t = Sc::tid() + i * Sc::size();
         if (t < total) {
             int b, q;
             bfly_map<BFAST, NQ>(t, nb, b, q);

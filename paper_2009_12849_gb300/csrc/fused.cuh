@@ -15,24 +15,23 @@
 // correction) in the order cols(0..L-1), cols(L), rows(0), cols(L+1), rows(1), ...
 // with the channel spectra in rings of `ring` levels.
 //
-// Every wait is bounded: after kSpinLimit polls the block latches bit 0 of the
+// Every wait is bounded: after p.spin_limit polls the block latches bit 0 of the
 // plan's error word (reported as a timeout) and carries on without waiting.
 #pragma once
 #include "persist.cuh"
 
 namespace mp {
 
-constexpr long long kSpinLimit = 1ll << 24;
-
-// Thread 0 waits until *ctr >= target (acquire); the block then synchronises.
-__device__ __forceinline__ void block_wait(const unsigned* ctr, unsigned target, int* err) {
+// Thread 0 waits until *ctr >= target (acquire), for at most `limit` polls
+// after the first; the block then synchronises.
+__device__ __forceinline__ void block_wait(const unsigned* ctr, unsigned target, int* err, long long limit) {
     if (threadIdx.x == 0) {
         long long spins = 0;
         while (true) {
             unsigned v;
             asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
             if (v >= target) break;
-            if (++spins > kSpinLimit) {
+            if (++spins > limit) {
                 atomicOr(err, 1);
                 break;
             }
@@ -194,11 +193,11 @@ __global__ void __launch_bounds__(256, 2) k_fwd_fused(ProjParams p) {
         const bool is_row = decode_lagged(t, nz, p.lag, A, B, &k, &idx);
         C* Tl = T + (size_t)(k % ring) * ny * nxp;
         if (is_row) {
-            if (k >= ring) block_wait(&cols_done[k - ring], (unsigned)B, p.err);
+            if (k >= ring) block_wait(&cols_done[k - ring], (unsigned)B, p.err, p.spin_limit);
             fwd_row_task<R, N>(p, k, idx * p.rows_fwd, Tl, buf);
             block_signal(&rows_done[k]);
         } else {
-            block_wait(&rows_done[k], (unsigned)A, p.err);
+            block_wait(&rows_done[k], (unsigned)A, p.err, p.spin_limit);
             fwd_col_task<R, N>(p, k, idx * p.tw_cols, Tl, buf);
             block_signal(&cols_done[k]);
         }
@@ -333,7 +332,7 @@ __global__ void __launch_bounds__(256, 2) k_inv_fused(ProjParams p) {
         if (is_col) {
             const int f = idx % nch;
             const int tile = idx / nch;
-            if (k >= ring) block_wait(&rows_done[(k - ring) * 4 + f], (unsigned)p.nrb_inv, p.err);
+            if (k >= ring) block_wait(&rows_done[(k - ring) * 4 + f], (unsigned)p.nrb_inv, p.err, p.spin_limit);
             if (!(f == 2 && k == 0)) {
                 C* dst = (f == 0) ? (C*)p.Tp : (f == 1) ? (C*)p.Tgy : (f == 2) ? (C*)p.Tgz : (C*)p.Tphi;
                 inv_col_task<R, N>(p, k, tile * p.tw_cols, f, dst + slot, buf);
@@ -342,7 +341,7 @@ __global__ void __launch_bounds__(256, 2) k_inv_fused(ProjParams p) {
         } else {
             const int ch = idx % nch;
             const int rb = idx / nch;
-            block_wait(&cols_done[k * 4 + ch], (unsigned)p.ntiles, p.err);
+            block_wait(&cols_done[k * 4 + ch], (unsigned)p.ntiles, p.err, p.spin_limit);
             const C* src = (ch == 0) ? (const C*)p.Tp : (ch == 1) ? (const C*)p.Tgy
                          : (ch == 2) ? (const C*)p.Tgz : (const C*)p.Tphi;
             inv_row_task<R, N>(p, k, rb * p.rows_inv, ch, src + slot, buf);

@@ -7,6 +7,7 @@
 //   spectral arrays  S, G, T, Tp, Tgy, Tgz, Tphi : [nz][ny][nxp], kx < nxh valid
 //   u, v, phi        : [nz][ny][nx] real;   w : [nz+1][ny][nx] real
 #pragma once
+#include "handoff.cuh"
 #include "fft.cuh"
 
 namespace mp {
@@ -59,6 +60,8 @@ struct ProjParams {
     int ntiles;                 // column tasks per level
     int bs_row;                 // smem stride of a row transform (complex elements)
     int bs_col;                 // smem stride of a column transform
+    HandoffArgs ho;             // hand-off of intermediates in L2 (pipelines); zero: none
+    long long spin_limit;       // polls before a bounded dependency wait gives up (timeout bit)
 };
 
 template <typename R> __device__ __forceinline__ const cplx<R>* ctab(const void* p) { return (const cplx<R>*)p; }
@@ -78,13 +81,13 @@ constexpr int kColTaskThreads = 256;
 // N > 0: compile-time in-place plan (one buffer); N == 0: run-time plan,
 // ping-pong with a second buffer right after the first.  Returns the buffer
 // holding the result.
-template <typename R, int N, int S>
+template <typename R, int N, int S, class Sc = BlockScope>
 __device__ __forceinline__ cplx<R>* run_fft(cplx<R>* buf, int nb, int bs, const FftFactors& f,
                                             const cplx<R>* __restrict__ tw) {
     if constexpr (N == 0) {
         return fft_batch<R, S>(buf, buf + nb * bs, nb, bs, f, tw);
     } else {
-        CtFFT<R, N, 1, S>::run(buf, nb, bs, tw);
+        CtFFT<R, N, 1, S, Sc>::run(buf, nb, bs, tw);
         return buf;
     }
 }
@@ -98,15 +101,16 @@ __device__ __forceinline__ cplx<R>* run_fft(cplx<R>* buf, int nb, int bs, const 
 // F is the field type: R, or double with R = float for the refinement passes
 // (the divergence is formed in F, then rounded to the transform precision).
 // ---------------------------------------------------------------------------
-template <typename R, int NX, typename F = R>
-__global__ void __launch_bounds__(512) k_fwd_rows(ProjParams p) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+// EF: u, v, w stream through L2 with evict-first priority (the pipelines,
+// whose x-spectra must stay resident until the column tasks read them).
+// One task: `rows` rows from j0 of level k, by the threads of scope Sc (the
+// block, or one warp with its own shared-memory slice at smem_raw).
+template <typename R, int NX, typename F, bool EF, class Sc>
+__device__ __forceinline__ void fwd_rows_task(const ProjParams& p, unsigned char* smem_raw, int k, int j0,
+                                              int rows) {
     using C = cplx<R>;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const int nrb = p.nrb_fwd;
-    const int k = blockIdx.x / nrb;
-    const int j0 = (blockIdx.x - k * nrb) * p.rows_fwd;
-    const int npair = p.rows_fwd / 2;
+    const int npair = rows / 2;
     const int bs = p.bs_row;
     C* bufA = (C*)smem_raw;
 
@@ -128,14 +132,25 @@ __global__ void __launch_bounds__(512) k_fwd_rows(ProjParams p) {
         // cells of a row and loads them as float4 (u, v, v of the row below,
         // w below and above), 4 groups in flight per thread.
         constexpr int G = 4, NG = NX / 4;
-        const int tot = p.rows_fwd * NG;
-        const int step = G * blockDim.x;
-        for (int base = threadIdx.x; base < tot; base += step) {
+        const int tot = rows * NG;
+        const int step = G * Sc::size();
+        // EF: u, v, w stream through L2 with evict-first priority, so that the
+        // x-spectra handed to the column tasks stay resident
+        const unsigned long long pol = EF ? l2_evict_first() : 0ull;
+        auto ld4 = [&](size_t o, const float* a) -> float4 {
+            if constexpr (EF) return ld_ef((const float4*)&a[o], pol);
+            else return *(const float4*)&a[o];
+        };
+        auto ld1 = [&](size_t o, const float* a) -> float {
+            if constexpr (EF) return ld_ef(&a[o], pol);
+            else return a[o];
+        };
+        for (int base = Sc::tid(); base < tot; base += step) {
             float4 u4[G], v4[G], vm4[G], wl4[G], wh4[G];
             float um1[G];
 #pragma unroll
             for (int c = 0; c < G; ++c) {
-                const int t = base + c * blockDim.x;
+                const int t = base + c * Sc::size();
                 const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
                 u4[c] = v4[c] = vm4[c] = wl4[c] = wh4[c] = z;
                 um1[c] = 0.f;
@@ -146,18 +161,18 @@ __global__ void __launch_bounds__(512) k_fwd_rows(ProjParams p) {
                     if (j < ny) {
                         const size_t row = (size_t)k * plane + (size_t)j * NX;
                         const size_t rowm = (size_t)k * plane + (size_t)(j == 0 ? ny - 1 : j - 1) * NX;
-                        u4[c] = *(const float4*)&u[row + i0];
-                        um1[c] = u[row + (i0 == 0 ? NX - 1 : i0 - 1)];
-                        v4[c] = *(const float4*)&v[row + i0];
-                        vm4[c] = *(const float4*)&v[rowm + i0];
-                        if (k > 0) wl4[c] = *(const float4*)&w[row + i0];
-                        if (k < nz - 1) wh4[c] = *(const float4*)&w[row + plane + i0];
+                        u4[c] = ld4(row + i0, u);
+                        um1[c] = i0 == 0 ? ld1(row + NX - 1, u) : u[row + i0 - 1];
+                        v4[c] = ld4(row + i0, v);
+                        vm4[c] = ld4(rowm + i0, v);
+                        if (k > 0) wl4[c] = ld4(row + i0, w);
+                        if (k < nz - 1) wh4[c] = ld4(row + plane + i0, w);
                     }
                 }
             }
 #pragma unroll
             for (int c = 0; c < G; ++c) {
-                const int t = base + c * blockDim.x;
+                const int t = base + c * Sc::size();
                 if (t < tot) {
                     const int r = t / NG;
                     const int i0 = 4 * (t - r * NG);
@@ -176,18 +191,18 @@ __global__ void __launch_bounds__(512) k_fwd_rows(ProjParams p) {
                 }
             }
         }
-        __syncthreads();
-        res = run_fft<R, NX, -1>(bufA, npair, bs, p.fx, ctab<R>(p.twx));
+        Sc::sync();
+        res = run_fft<R, NX, -1, Sc>(bufA, npair, bs, p.fx, ctab<R>(p.twx));
     } else {
         // Loads are batched (kLoadBatch elements per thread issued before any is
         // used) so that enough bytes are in flight to cover DRAM latency.
-        const int tot = p.rows_fwd * nx;
-        const int step = kLoadBatch * blockDim.x;
-        for (int base = threadIdx.x; base < tot; base += step) {
+        const int tot = rows * nx;
+        const int step = kLoadBatch * Sc::size();
+        for (int base = Sc::tid(); base < tot; base += step) {
             F uc[kLoadBatch], um[kLoadBatch], vc[kLoadBatch], vm[kLoadBatch], wl[kLoadBatch], wh[kLoadBatch];
 #pragma unroll
             for (int c = 0; c < kLoadBatch; ++c) {
-                const int t = base + c * blockDim.x;
+                const int t = base + c * Sc::size();
                 uc[c] = um[c] = vc[c] = vm[c] = wl[c] = wh[c] = (F)0;
                 if (t < tot) {
                     const int r = (NX > 0) ? t / NX : t / nx;
@@ -208,7 +223,7 @@ __global__ void __launch_bounds__(512) k_fwd_rows(ProjParams p) {
             }
 #pragma unroll
             for (int c = 0; c < kLoadBatch; ++c) {
-                const int t = base + c * blockDim.x;
+                const int t = base + c * Sc::size();
                 if (t < tot) {
                     const int r = (NX > 0) ? t / NX : t / nx;
                     const int i = t - r * nx;
@@ -227,8 +242,8 @@ __global__ void __launch_bounds__(512) k_fwd_rows(ProjParams p) {
                 }
             }
         }
-        __syncthreads();
-        res = run_fft<R, NX, -1>(bufA, npair, bs, p.fx, ctab<R>(p.twx));
+        Sc::sync();
+        res = run_fft<R, NX, -1, Sc>(bufA, npair, bs, p.fx, ctab<R>(p.twx));
     }
 
     C* T = (C*)p.T;
@@ -239,7 +254,7 @@ __global__ void __launch_bounds__(512) k_fwd_rows(ProjParams p) {
         const C* rq = res + q * bs;
         C* to = T + ((size_t)k * ny + j) * p.nxp;
         const bool second = j + 1 < ny;
-        for (int kx = threadIdx.x; kx < nxh; kx += blockDim.x) {
+        for (int kx = Sc::tid(); kx < nxh; kx += Sc::size()) {
             const C z = rq[spad(kx)];
             const C zc = cconj(rq[spad(kx == 0 ? 0 : nx - kx)]);
             const C a = cscale(cadd(z, zc), (R)0.5);
@@ -248,6 +263,15 @@ __global__ void __launch_bounds__(512) k_fwd_rows(ProjParams p) {
             if (second) to[kx + p.nxp] = cmk<R>((R)0.5 * dd.y, (R)-0.5 * dd.x);
         }
     }
+}
+
+template <typename R, int NX, typename F = R, bool EF = false>
+__global__ void __launch_bounds__(512) k_fwd_rows(ProjParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nrb = p.nrb_fwd;
+    const int kl = blockIdx.x / nrb;
+    fwd_rows_task<R, NX, F, EF, BlockScope>(p, smem_raw, kl, (blockIdx.x - kl * nrb) * p.rows_fwd,
+                                            p.rows_fwd);
 }
 
 // ---------------------------------------------------------------------------
@@ -298,36 +322,88 @@ __device__ __forceinline__ void store_cols(cplx<R>* dst, const cplx<R>* buf, int
     }
 }
 
+// Chained forward columns: the tiles whose columns share 128-byte lines of T
+// (16 complex FP32 values) count their reads in p.ho.groups; the last tile of
+// a group to finish reading discards the group's lines of the level.  Tiles
+// of 16 or more columns own their lines and discard them at once.
+template <typename R>
+__device__ __forceinline__ void discard_fwd_tile(const ProjParams& p, int k, int tile) {
+    constexpr int LINE = 128 / (int)sizeof(cplx<R>);       // complex values per line
+    const int tw = p.tw_cols;
+    int c0, nc;                                             // first column, columns to discard
+    if (tw >= LINE) {
+        // the last tile may reach past the padded row: its lines stop at nxp
+        c0 = tile * tw;
+        nc = min(tw, p.nxp - c0);
+        if (nc <= 0) return;
+    } else {
+        __shared__ unsigned s_last;
+        const int g = LINE / tw;                            // tiles per line group
+        const int grp = tile / g;
+        const int members = min(g, p.ntiles - grp * g);
+        if (threadIdx.x == 0) {
+            unsigned last = 1;
+            if (members > 1) {
+                __threadfence();
+                const int ngrp = (p.ntiles + g - 1) / g;
+                last = (atomicAdd(&p.ho.groups[(size_t)k * ngrp + grp], 1u) + 1u) % (unsigned)members == 0;
+            }
+            s_last = last;
+        }
+        __syncthreads();
+        if (!s_last) return;
+        c0 = grp * LINE;
+        nc = LINE;
+    }
+    const cplx<R>* T = (const cplx<R>*)p.T + (size_t)k * p.ny * p.nxp;
+    const int lpr = nc / LINE;                              // lines per row
+    for (int t = threadIdx.x; t < p.ny * lpr; t += blockDim.x) {
+        const int j = t / lpr;
+        l2_discard(T + (size_t)j * p.nxp + c0 + (t - j * lpr) * LINE);
+    }
+}
+
+// One column task of a compile-time length: tile `tile` of level k, T -> S.
 template <typename R, int NY>
-__global__ void __launch_bounds__(512) k_fwd_cols(ProjParams p) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void fwd_cols_task(const ProjParams& p, unsigned char* smem_raw, int k, int tile) {
     using C = cplx<R>;
-    const int k = blockIdx.x / p.ntiles;
-    const int kx0 = (blockIdx.x - k * p.ntiles) * p.tw_cols;
+    const int kx0 = tile * p.tw_cols;
     C* buf = (C*)smem_raw;
     const C* T = (const C*)p.T;
     C* S = (C*)p.S;
     const int nxh = p.nxh, nxp = p.nxp, ny = p.ny;
-    if constexpr (NY > 0) {
-        auto load = [&](int c, int j) -> C {
-            const int kx = kx0 + c;
-            return (kx < nxh) ? T[((size_t)k * ny + j) * nxp + kx] : cmk<R>((R)0, (R)0);
-        };
-        ct_first<R, NY, -1, true>(buf, p.tw_cols, p.bs_col, load);
-        CtMid<R, NY, StageInfo<R, NY, 1>::NEXT, -1>::run(buf, p.tw_cols, p.bs_col, ctab<R>(p.twy));
-        auto store = [&](int c, int q, const C* x, int ns) {
-            const int kx = kx0 + c;
-            if (kx >= nxh) return;
-            constexpr int RAD = StageInfo<R, NY, LastNs<R, NY>::value>::RAD;
+    auto load = [&](int c, int j) -> C {
+        const int kx = kx0 + c;
+        return (kx < nxh) ? T[((size_t)k * ny + j) * nxp + kx] : cmk<R>((R)0, (R)0);
+    };
+    ct_first<R, NY, -1, true>(buf, p.tw_cols, p.bs_col, load);
+    if (p.ho.discard) discard_fwd_tile<R>(p, k, tile);
+    CtMid<R, NY, StageInfo<R, NY, 1>::NEXT, -1>::run(buf, p.tw_cols, p.bs_col, ctab<R>(p.twy));
+    auto store = [&](int c, int q, const C* x, int ns) {
+        const int kx = kx0 + c;
+        if (kx >= nxh) return;
+        constexpr int RAD = StageInfo<R, NY, LastNs<R, NY>::value>::RAD;
 #pragma unroll
-            for (int r = 0; r < RAD; ++r) S[((size_t)k * ny + q + r * ns) * nxp + kx] = x[r];
-        };
-        ct_last<R, NY, -1, true>(buf, p.tw_cols, p.bs_col, ctab<R>(p.twy), store);
+        for (int r = 0; r < RAD; ++r) S[((size_t)k * ny + q + r * ns) * nxp + kx] = x[r];
+    };
+    ct_last<R, NY, -1, true>(buf, p.tw_cols, p.bs_col, ctab<R>(p.twy), store);
+}
+
+template <typename R, int NY>
+__global__ void __launch_bounds__(512) k_fwd_cols(ProjParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using C = cplx<R>;
+    const int kl = blockIdx.x / p.ntiles;
+    const int k = kl;
+    const int tile = blockIdx.x - kl * p.ntiles;
+    if constexpr (NY > 0) {
+        fwd_cols_task<R, NY>(p, smem_raw, k, tile);
     } else {
-        load_cols<R>(buf, T, k, kx0, p, nullptr);
+        C* buf = (C*)smem_raw;
+        load_cols<R>(buf, (const C*)p.T, k, tile * p.tw_cols, p, nullptr);
         __syncthreads();
         const C* res = run_fft<R, NY, -1>(buf, p.tw_cols, p.bs_col, p.fy, ctab<R>(p.twy));
-        store_cols<R>(S, res, k, kx0, p);
+        store_cols<R>((C*)p.S, res, k, tile * p.tw_cols, p);
     }
 }
 
@@ -676,6 +752,28 @@ __device__ __forceinline__ void inv_cols_ct_task(const ProjParams& p, int k, int
     ct_last<R, NY, 1, true>(buf, p.tw_cols, p.bs_col, ctab<R>(p.twy), store);
 }
 
+// One column task of a compile-time length: tile from kx0 of level k; kind
+// 0 transforms the p^ tile (x- and y-gradient, and phi if requested; with
+// PHI the potential alone), kind 1 the gz^ tile.
+template <typename R, int NY, bool PHI>
+__device__ __forceinline__ void inv_cols_tile(const ProjParams& p, unsigned char* smem_raw, int k, int kx0,
+                                              int kind) {
+    cplx<R>* buf = (cplx<R>*)smem_raw;
+    if constexpr (PHI) {
+        if (kind == 0) inv_cols_ct_task<R, NY>(p, k, kx0, 3, buf);
+    } else if (kind == 0) {
+        inv_cols_ct_task<R, NY>(p, k, kx0, 0, buf);
+        __syncthreads();
+        inv_cols_ct_task<R, NY>(p, k, kx0, 1, buf);
+        if (p.nch == 4) {
+            __syncthreads();
+            inv_cols_ct_task<R, NY>(p, k, kx0, 3, buf);
+        }
+    } else if (k > 0) {
+        inv_cols_ct_task<R, NY>(p, k, kx0, 2, buf);
+    }
+}
+
 // PHI: the potential alone (refinement passes): kind 0 transforms the p^ tile
 // into Tphi, kind 1 does nothing.
 template <typename R, int NY, bool PHI = false>
@@ -683,24 +781,9 @@ __global__ void __launch_bounds__(512) k_inv_cols(ProjParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using C = cplx<R>;
     if constexpr (NY > 0) {
-        const int kind = blockIdx.x & 1;
         const int task = blockIdx.x >> 1;
-        const int k = task / p.ntiles;
-        const int kx0 = (task - k * p.ntiles) * p.tw_cols;
-        C* buf = (C*)smem_raw;
-        if constexpr (PHI) {
-            if (kind == 0) inv_cols_ct_task<R, NY>(p, k, kx0, 3, buf);
-        } else if (kind == 0) {
-            inv_cols_ct_task<R, NY>(p, k, kx0, 0, buf);
-            __syncthreads();
-            inv_cols_ct_task<R, NY>(p, k, kx0, 1, buf);
-            if (p.nch == 4) {
-                __syncthreads();
-                inv_cols_ct_task<R, NY>(p, k, kx0, 3, buf);
-            }
-        } else if (k > 0) {
-            inv_cols_ct_task<R, NY>(p, k, kx0, 2, buf);
-        }
+        const int kl = task / p.ntiles;
+        inv_cols_tile<R, NY, PHI>(p, smem_raw, kl, (task - kl * p.ntiles) * p.tw_cols, blockIdx.x & 1);
         return;
     }
     const int nf = p.nch;
@@ -767,7 +850,123 @@ __device__ __forceinline__ cplx<R> inv_spectrum(const ProjParams& p, int k, int 
 // Generic lengths: all channels of a row block in one task.  F is the field
 // type (R, or double with R = float for the refinement passes: the gradient
 // is subtracted from the FP64 field in FP64).
-template <typename R, int NX, typename F = R>
+// Compile-time length along x: one channel of one row pair per task (the
+// body of k_inv_rows; returns early for the bottom face of w).
+template <typename R, int NX, typename F, bool EF, class Sc>
+__device__ __forceinline__ void inv_rows_ct(const ProjParams& p, unsigned char* smem_raw, int k, int j0, int ch,
+                                            int rows) {
+    using C = cplx<R>;
+    const int ny = p.ny, nz = p.nz;
+    const int bs = p.bs_row;
+    C* bufA = (C*)smem_raw;
+    const size_t plane = (size_t)ny * NX;
+    constexpr int NXH = NX / 2 + 1;
+    const int npr = rows / 2;                    // transforms (row pairs) per task
+    F* out = (ch == 0) ? (F*)p.uo : (ch == 1) ? (F*)p.vo : (ch == 2) ? (F*)p.wo : (F*)p.phi;
+    if (ch == 2 && k == 0) {
+        // bottom face: w = 0
+        for (int t = Sc::tid(); t < rows * NX; t += Sc::size()) {
+            const int j = j0 + t / NX;
+            if (j < ny) {
+                out[(size_t)j * NX + (t % NX)] = (F)0;
+                if (nz == 1) out[plane + (size_t)j * NX + (t % NX)] = (F)0;   // top face too
+            }
+        }
+        return;
+    }
+    const F* in = (ch == 0) ? (const F*)p.u : (ch == 1) ? (const F*)p.v : (const F*)p.w;
+    const bool upd = ch < 3;
+    const C* spec = inv_channel_spectrum<R>(p, ch) + (size_t)k * ny * p.nxp;
+    const int nxp = p.nxp;
+    auto load = [&](int b, int kx) -> C {
+        const int j = j0 + 2 * b;
+        C a = cmk<R>((R)0, (R)0), c = cmk<R>((R)0, (R)0);
+        if (j < ny) a = hermitian_at<R>(spec + (size_t)j * nxp, NX, NXH, kx);
+        if (j + 1 < ny) c = hermitian_at<R>(spec + (size_t)(j + 1) * nxp, NX, NXH, kx);
+        return cmk<R>(a.x - c.y, a.y + c.x);
+    };
+    ct_first<R, NX, 1, false, false, Sc>(bufA, npr, bs, load);
+    if (p.ho.discard) {
+        // pipelines: this task is the only reader of its rows of the channel
+        // spectrum; the lines are dead once the first stage has read them
+        constexpr int LINE = 128 / (int)sizeof(C);
+        const int lpr = nxp / LINE;
+        for (int t = Sc::tid(); t < rows * lpr; t += Sc::size()) {
+            const int r = t / lpr;
+            if (j0 + r < ny) l2_discard(spec + (size_t)(j0 + r) * nxp + (t - r * lpr) * LINE);
+        }
+    }
+    CtMid<R, NX, StageInfo<R, NX, 1>::NEXT, 1, Sc>::run(bufA, npr, bs, ctab<R>(p.twx));
+    // the correction reads u, v or w where it writes them (outputs may
+    // alias inputs)
+    constexpr int LRAD = StageInfo<R, NX, LastNs<R, NX>::value>::RAD;
+    if constexpr (sizeof(F) == sizeof(R)) {
+        // every value this thread will update is loaded before the last
+        // stage writes any
+        constexpr int LNB = (ElemsPerThread<R>::value + LRAD - 1) / LRAD;
+        F prev[LNB][2][LRAD];
+        // EF: u, v, w stream through L2 with evict-first priority
+        constexpr bool ef = EF && sizeof(F) == 4;
+        const unsigned long long pol = ef ? l2_evict_first() : 0ull;
+        auto pre = [&](int b, int q, int ns, int i) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = j0 + 2 * b + h;
+                const size_t row = (size_t)k * plane + (size_t)j * NX + q;
+#pragma unroll
+                for (int r = 0; r < LRAD; ++r) {
+                    F val = (F)0;
+                    if (upd && j < ny) {
+                        if constexpr (ef) val = ld_ef((const float*)&in[row + r * ns], pol);
+                        else val = in[row + r * ns];
+                    }
+                    prev[i][h][r] = val;
+                }
+            }
+        };
+        auto store = [&](int b, int q, const C* x, int ns, int i) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = j0 + 2 * b + h;
+                if (j >= ny) continue;
+                const size_t row = (size_t)k * plane + (size_t)j * NX + q;
+#pragma unroll
+                for (int r = 0; r < LRAD; ++r) {
+                    const F val = (F)(h ? x[r].y : x[r].x);
+                    const F res = (ch < 3) ? prev[i][h][r] - val : (upd ? prev[i][h][r] + val : val);
+                    if constexpr (ef) st_ef((float*)&out[row + r * ns], res, pol);
+                    else out[row + r * ns] = res;
+                    if (ch == 2 && k == nz - 1) out[row + r * ns + plane] = (F)0;
+                }
+            }
+        };
+        ct_last_pre<R, NX, 1, false, Sc>(bufA, npr, bs, ctab<R>(p.twx), pre, store);
+    } else {
+        // wider fields (refinement passes): one butterfly's operands at a
+        // time, which keeps the FP64 values in registers
+        auto store = [&](int b, int q, const C* x, int ns) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = j0 + 2 * b + h;
+                if (j >= ny) continue;
+                const size_t row = (size_t)k * plane + (size_t)j * NX + q;
+                F prev[LRAD];
+#pragma unroll
+                for (int r = 0; r < LRAD; ++r) prev[r] = upd ? in[row + r * ns] : (F)0;
+#pragma unroll
+                for (int r = 0; r < LRAD; ++r) {
+                    const F val = (F)(h ? x[r].y : x[r].x);
+                    out[row + r * ns] = (ch < 3) ? prev[r] - val : (upd ? prev[r] + val : val);
+                    if (ch == 2 && k == nz - 1) out[row + r * ns + plane] = (F)0;
+                }
+            }
+        };
+        ct_last<R, NX, 1, false, Sc>(bufA, npr, bs, ctab<R>(p.twx), store);
+    }
+}
+
+// EF: u, v, w stream through L2 with evict-first priority (pipelines).
+template <typename R, int NX, typename F = R, bool EF = false>
 __global__ void __launch_bounds__(512) k_inv_rows(ProjParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using C = cplx<R>;
@@ -778,91 +977,12 @@ __global__ void __launch_bounds__(512) k_inv_rows(ProjParams p) {
     C* bufA = (C*)smem_raw;
     const size_t plane = (size_t)ny * nx;
     if constexpr (NX > 0) {
-        constexpr int NXH = NX / 2 + 1;
+        const int nrb = p.nrb_inv;
         const int ch = p.phi_only ? 3 : blockIdx.x % nch;
         const int t2 = blockIdx.x / nch;
-        const int k = t2 / nrb;
-        const int j0 = (t2 - k * nrb) * p.rows_inv;
-        const int npr = p.rows_inv / 2;              // transforms (row pairs) per task
-        F* out = (ch == 0) ? (F*)p.uo : (ch == 1) ? (F*)p.vo : (ch == 2) ? (F*)p.wo : (F*)p.phi;
-        if (ch == 2 && k == 0) {
-            // bottom face: w = 0
-            for (int t = threadIdx.x; t < p.rows_inv * NX; t += blockDim.x) {
-                const int j = j0 + t / NX;
-                if (j < ny) {
-                    out[(size_t)j * NX + (t % NX)] = (F)0;
-                    if (nz == 1) out[plane + (size_t)j * NX + (t % NX)] = (F)0;   // top face too
-                }
-            }
-            return;
-        }
-        const F* in = (ch == 0) ? (const F*)p.u : (ch == 1) ? (const F*)p.v : (const F*)p.w;
-        const bool upd = ch < 3;
-        const C* spec = inv_channel_spectrum<R>(p, ch) + (size_t)k * ny * p.nxp;
-        const int nxp = p.nxp;
-        auto load = [&](int b, int kx) -> C {
-            const int j = j0 + 2 * b;
-            C a = cmk<R>((R)0, (R)0), c = cmk<R>((R)0, (R)0);
-            if (j < ny) a = hermitian_at<R>(spec + (size_t)j * nxp, NX, NXH, kx);
-            if (j + 1 < ny) c = hermitian_at<R>(spec + (size_t)(j + 1) * nxp, NX, NXH, kx);
-            return cmk<R>(a.x - c.y, a.y + c.x);
-        };
-        ct_first<R, NX, 1, false>(bufA, npr, bs, load);
-        CtMid<R, NX, StageInfo<R, NX, 1>::NEXT, 1>::run(bufA, npr, bs, ctab<R>(p.twx));
-        // the correction reads u, v or w where it writes them (outputs may
-        // alias inputs)
-        constexpr int LRAD = StageInfo<R, NX, LastNs<R, NX>::value>::RAD;
-        if constexpr (sizeof(F) == sizeof(R)) {
-            // every value this thread will update is loaded before the last
-            // stage writes any
-            constexpr int LNB = (ElemsPerThread<R>::value + LRAD - 1) / LRAD;
-            F prev[LNB][2][LRAD];
-            auto pre = [&](int b, int q, int ns, int i) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int j = j0 + 2 * b + h;
-                    const size_t row = (size_t)k * plane + (size_t)j * NX + q;
-#pragma unroll
-                    for (int r = 0; r < LRAD; ++r) prev[i][h][r] = (upd && j < ny) ? in[row + r * ns] : (F)0;
-                }
-            };
-            auto store = [&](int b, int q, const C* x, int ns, int i) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int j = j0 + 2 * b + h;
-                    if (j >= ny) continue;
-                    const size_t row = (size_t)k * plane + (size_t)j * NX + q;
-#pragma unroll
-                    for (int r = 0; r < LRAD; ++r) {
-                        const F val = (F)(h ? x[r].y : x[r].x);
-                        out[row + r * ns] = (ch < 3) ? prev[i][h][r] - val : (upd ? prev[i][h][r] + val : val);
-                        if (ch == 2 && k == nz - 1) out[row + r * ns + plane] = (F)0;
-                    }
-                }
-            };
-            ct_last_pre<R, NX, 1, false>(bufA, npr, bs, ctab<R>(p.twx), pre, store);
-        } else {
-            // wider fields (refinement passes): one butterfly's operands at a
-            // time, which keeps the FP64 values in registers
-            auto store = [&](int b, int q, const C* x, int ns) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int j = j0 + 2 * b + h;
-                    if (j >= ny) continue;
-                    const size_t row = (size_t)k * plane + (size_t)j * NX + q;
-                    F prev[LRAD];
-#pragma unroll
-                    for (int r = 0; r < LRAD; ++r) prev[r] = upd ? in[row + r * ns] : (F)0;
-#pragma unroll
-                    for (int r = 0; r < LRAD; ++r) {
-                        const F val = (F)(h ? x[r].y : x[r].x);
-                        out[row + r * ns] = (ch < 3) ? prev[r] - val : (upd ? prev[r] + val : val);
-                        if (ch == 2 && k == nz - 1) out[row + r * ns + plane] = (F)0;
-                    }
-                }
-            };
-            ct_last<R, NX, 1, false>(bufA, npr, bs, ctab<R>(p.twx), store);
-        }
+        const int kl = t2 / nrb;
+        inv_rows_ct<R, NX, F, EF, BlockScope>(p, smem_raw, kl, (t2 - kl * nrb) * p.rows_inv, ch,
+                                              p.rows_inv);
     } else {
         const int k = blockIdx.x / nrb;
         const int j0 = (blockIdx.x - k * nrb) * p.rows_inv;

@@ -17,11 +17,13 @@
 
 #include "krylov.h"
 #include "pickers.h"
+#include "pipe.cuh"
 
 using namespace mp;
 
 struct monc_proj_plan_s {
     int nx, ny, nz, nxh, nxp, precision;
+    int precision_api;                    // as requested (MONC_PROJ_MIXED_Z64 runs as MONC_PROJ_MIXED)
     double dx, dy;
     FftFactors fx, fy;
     int device;
@@ -58,6 +60,15 @@ struct monc_proj_plan_s {
     size_t off_sync, sync_bytes;
     int bs_row, bs_col;
     size_t smem_fwd_rows, smem_cols, smem_fcols, smem_inv_rows[2];
+    bool pipe;                            // persistent pipelines of the transforms (pipe.cuh), opt-in
+    long long spin_limit;                 // polls before a bounded dependency wait gives up
+    monc_proj_free_fn tables_free;        // how dev_tables is released (NULL: cudaFree)
+    void* tables_user;
+    bool pipe_ef;                         // their evict-first variants
+    int pipe_lag_fwd, pipe_lag_inv;       // their producer/consumer lags in levels
+    int grid_fwd_pipe, grid_inv_pipe;     // their grids (resident blocks)
+    size_t smem_pipe;
+    size_t off_groups, groups_bytes;      // pipelines: per (level, line group) counters of the hand-off
     // workspace layout
     size_t ws_bytes;
     size_t off_S, off_G, off_T, off_Tp, off_Tgy, off_Tgz, off_Tphi, off_Y, off_Gp, off_phipass, off_phimean;
@@ -70,9 +81,9 @@ struct monc_proj_plan_s {
 
 namespace {
 
-constexpr int kPhases = 7;
+constexpr int kPhases = 9;
 const char* const kPhaseNames[kPhases] = {"fwd_rows", "fwd_cols", "tridiag", "inv_cols", "inv_rows",
-                                          "fwd_fused", "inv_fused"};
+                                          "fwd_fused", "inv_fused", "fwd_pipe", "inv_pipe"};
 
 // Start/end events of every phase of one recorded solve (null when not recording).
 struct PhaseMarks {
@@ -167,6 +178,25 @@ int env_int(const char* name, int dflt) {
     return (e && *e) ? std::max(1, std::atoi(e)) : dflt;
 }
 
+// As env_int, but 0 is allowed.
+long long env_ll0(const char* name, long long dflt) {
+    const char* e = std::getenv(name);
+    return (e && *e) ? std::max(0ll, std::atoll(e)) : dflt;
+}
+
+// Polls of a bounded dependency wait (pipelines, fused kernels) before it
+// gives up and latches the timeout bit, about a second at the 64 ns poll
+// interval; MONC_PROJ_SPIN_LIMIT, read when the plan is made, overrides it
+// (0 gives up at the first poll that finds the dependency unmet, which lets
+// a test drive the timeout path without hanging anything).
+constexpr long long kSpinLimit = 1ll << 24;
+
+// Process-wide allocator of plan tables (monc_proj_set_allocator).
+std::mutex g_alloc_mu;
+monc_proj_alloc_fn g_alloc = nullptr;
+monc_proj_free_fn g_free = nullptr;
+void* g_alloc_user = nullptr;
+
 // The fused persistent kernels are opt-in (MONC_PROJ_FUSED=1 in the
 // environment; MONC_PROJ_FUSED_LAG and MONC_PROJ_FUSED_RING set the
 // producer/consumer lag and the ring depth in levels): on GB300 they measured
@@ -184,6 +214,20 @@ int threads_for(int elems, int E) {
 }
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+// Persistent pipelines (pipe.cuh) replace the four transform launches of
+// mixed plans on square grids of 256, 512 or 1024 when MONC_PROJ_PIPE=1 (read
+// when the plan is made): they hand the intermediate spectra over in L2 and
+// cut the DRAM traffic of the transforms to the fields and D^, but measured
+// slower than the one-launch-per-pass kernels, whose time is set by
+// instruction issue rather than DRAM.  Lags in levels: the forward pass has
+// about 130 tasks per level of 1024^2, the inverse 320.
+constexpr int kPipeLagFwd = 4;
+constexpr int kPipeLagInv = 2;
+bool pipe_enabled() {
+    const char* e = std::getenv("MONC_PROJ_PIPE");
+    return e && e[0] == '1';
+}
 
 // exp(-2 pi i m / n): *c = cos(2 pi m/n), *s = -sin(2 pi m/n).  The angle is
 // reduced exactly (integer arithmetic) to [0, pi/4] before libm is called.
@@ -276,6 +320,7 @@ ProjParams make_params(const monc_proj_plan_s* p, const void* u, const void* v, 
     q.tw_cols = p->tw_cols; q.ntiles = p->ntiles;
     q.bs_row = p->bs_row; q.bs_col = p->bs_col;
     q.nch = phi ? 4 : 3;
+    q.spin_limit = p->spin_limit;
     q.rows_inv = p->rows_inv[q.nch == 4 ? 1 : 0];
     q.nrb_inv = (p->ny + q.rows_inv - 1) / q.rows_inv;
     return q;
@@ -373,12 +418,44 @@ bool launch_cols_tma(const monc_proj_plan_s* p, const ProjParams& q, bool inv, c
     return true;
 }
 
+// Forward pipeline, vertical solve, inverse pipeline (pipe.cuh).
+int launch_piped(monc_proj_plan_s* p, const ProjParams& q, cudaStream_t st, const PhaseMarks& pm) {
+    const int nz = p->nz;
+    unsigned* groups = (unsigned*)((unsigned char*)q.S - p->off_S + p->off_groups);
+    if (cudaMemsetAsync(q.sync, 0, (size_t)(2 + 2 * nz) * sizeof(unsigned), st) != cudaSuccess ||
+        cudaMemsetAsync(groups, 0, p->groups_bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        return MONC_PROJ_ECUDA;
+    }
+    ProjParams qp = q;
+    qp.ho.discard = 1;
+    qp.ho.groups = groups;
+    const long long per_fwd = (long long)nz * ((p->ny + 1) / 2 + p->ntiles);
+    const long long per_inv = (long long)nz * (2 * p->ntiles + p->ny);
+    pm.start(7, st);
+    qp.lag = p->pipe_lag_fwd;
+    pick_fwd_pipe(p->nx, p->ny, p->pipe_ef)<<<(unsigned)std::min<long long>(p->grid_fwd_pipe, per_fwd), kPipeThreads, p->smem_pipe,
+                                  st>>>(qp);
+    pm.end(7, st);
+    const long long ncol = (long long)p->ny * ((p->nxh + 31) & ~31);
+    pm.start(2, st);
+    pick_tridiag<float>()<<<(unsigned)((ncol + kTriThreads - 1) / kTriThreads), kTriThreads, 0, st>>>(q);
+    pm.end(2, st);
+    pm.start(8, st);
+    qp.lag = p->pipe_lag_inv;
+    pick_inv_pipe(p->nx, p->ny, p->pipe_ef)<<<(unsigned)std::min<long long>(p->grid_inv_pipe, per_inv), kPipeThreads, p->smem_pipe,
+                                  st>>>(qp);
+    pm.end(8, st);
+    return cudaGetLastError() == cudaSuccess ? MONC_PROJ_OK : MONC_PROJ_ECUDA;
+}
+
 template <typename R>
 int launch_solve(monc_proj_plan_s* p, const ProjParams& q, cudaStream_t st) {
     const int nz = p->nz;
     const int inv_idx = (q.nch == 4) ? 1 : 0;
     const PhaseMarks pm = begin_marks(p);
     const long long ncol = (long long)p->ny * ((p->nxh + 31) & ~31);
+    if (p->pipe && sizeof(R) == 4) return launch_piped(p, q, st, pm);
     if (p->fused) {
         if (cudaMemsetAsync(q.sync, 0, p->sync_bytes, st) != cudaSuccess) { cudaGetLastError(); return MONC_PROJ_ECUDA; }
         pm.start(5, st);
@@ -527,9 +604,34 @@ int setup_fused(monc_proj_plan_s* p) {
     return MONC_PROJ_OK;
 }
 
+// Pipelines: raise their shared-memory limits and size their grids to the
+// blocks that fit the device at once (the schedule needs no residency, but
+// more blocks than fit would only wait for a slot).
+int setup_pipe(monc_proj_plan_s* p) {
+    const KernelFn ff = pick_fwd_pipe(p->nx, p->ny, p->pipe_ef), fi = pick_inv_pipe(p->nx, p->ny, p->pipe_ef);
+    if (!ff || !fi || p->smem_pipe > kSmemMax || p->thr_cols != kPipeThreads) { p->pipe = false; return MONC_PROJ_OK; }
+    int bf = 0, bi = 0;
+    if (cudaFuncSetAttribute((const void*)ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_pipe) != cudaSuccess ||
+        cudaFuncSetAttribute((const void*)fi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_pipe) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, (const void*)ff, kPipeThreads, p->smem_pipe) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bi, (const void*)fi, kPipeThreads, p->smem_pipe) != cudaSuccess) {
+        cudaGetLastError();
+        return MONC_PROJ_ECUDA;
+    }
+    if (bf < 1 || bi < 1) { p->pipe = false; return MONC_PROJ_OK; }
+    p->grid_fwd_pipe = bf * p->nsm;
+    p->grid_inv_pipe = bi * p->nsm;
+    return MONC_PROJ_OK;
+}
+
 int plan_kernel_attrs(monc_proj_plan_s* p) {
     const int r = p->precision == MONC_PROJ_FP64 ? set_kernel_attrs<double>(p) : set_kernel_attrs<float>(p);
-    if (r != MONC_PROJ_OK || !p->fused) return r;
+    if (r != MONC_PROJ_OK) return r;
+    if (p->pipe) {
+        const int rp = setup_pipe(p);
+        if (rp != MONC_PROJ_OK) return rp;
+    }
+    if (!p->fused) return MONC_PROJ_OK;
     return p->precision == MONC_PROJ_FP64 ? setup_fused<double>(p) : setup_fused<float>(p);
 }
 
@@ -537,7 +639,8 @@ int plan_kernel_attrs(monc_proj_plan_s* p) {
 int validate_grid(int nx, int ny, int nz, double dx, double dy, const double* dz,
                   const double* rho_c, const double* rho_f, int precision) {
     if (nx < 1 || ny < 1 || nz < 1 || !dz || !rho_c || !rho_f) return MONC_PROJ_EINVAL;
-    if (precision != MONC_PROJ_FP64 && precision != MONC_PROJ_MIXED && precision != MONC_PROJ_REFINED)
+    if (precision != MONC_PROJ_FP64 && precision != MONC_PROJ_MIXED && precision != MONC_PROJ_REFINED &&
+        precision != MONC_PROJ_MIXED_Z64)
         return MONC_PROJ_EINVAL;
     if (!finite_pos(dx) || !finite_pos(dy)) return MONC_PROJ_EINVAL;
     for (int k = 0; k < nz; ++k)
@@ -613,8 +716,12 @@ void set_task_shapes(monc_proj_plan_s* p) {
 }
 
 void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double dy,
-                  const double* dz, const double* rho_c, const double* rho_f, int precision,
+                  const double* dz, const double* rho_c, const double* rho_f, int precision_api,
                   std::vector<unsigned char>& blob, TableOffsets& to) {
+    // MONC_PROJ_MIXED_Z64 is a mixed plan whose every column runs a3 in FP64
+    const bool z64 = precision_api == MONC_PROJ_MIXED_Z64;
+    const int precision = z64 ? MONC_PROJ_MIXED : precision_api;
+    p->precision_api = precision_api;
     p->nx = nx; p->ny = ny; p->nz = nz; p->dx = dx; p->dy = dy; p->precision = precision;
     p->nxh = nx / 2 + 1;
     p->nxp = (p->nxh + 3) & ~3;
@@ -663,7 +770,7 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     // v_max = max_k 2 (A[k] + A[k+1]) / (rho_c dz)[k] run in FP64.
     double vmax = 0.0;
     for (int k = 0; k < nz; ++k) vmax = std::max(vmax, 2.0 * (acoef[k] + acoef[k + 1]) / svol[k]);
-    p->lam_fp64 = (precision == MONC_PROJ_FP64) ? INFINITY : kFp64Fraction * vmax;
+    p->lam_fp64 = (precision == MONC_PROJ_FP64 || z64) ? INFINITY : kFp64Fraction * vmax;
     {
         const int nxw = (p->nxh + 31) & ~31;
         long long n64 = 0;
@@ -756,6 +863,20 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     p->lag = std::min(nz, env_int("MONC_PROJ_FUSED_LAG", 3));
     if (p->fused) p->ring = std::min(nz, std::max(p->lag + 1, env_int("MONC_PROJ_FUSED_RING", p->lag + 3)));
 
+    // the pipelines' consumers discard whole 128-byte lines of the
+    // intermediate spectra, so rows are padded to whole lines
+    p->pipe = precision == MONC_PROJ_MIXED && ctx && cty && !p->persist_cols && !p->tma_cols && !p->fused &&
+              pick_fwd_pipe(nx, ny) && pick_inv_pipe(nx, ny) && pipe_enabled();
+    p->pipe_lag_fwd = (int)std::min<long long>(nz, env_ll0("MONC_PROJ_PIPE_LAG_FWD", kPipeLagFwd));
+    p->pipe_lag_inv = (int)std::min<long long>(nz, env_ll0("MONC_PROJ_PIPE_LAG_INV", kPipeLagInv));
+    p->spin_limit = env_ll0("MONC_PROJ_SPIN_LIMIT", kSpinLimit);
+    {
+        const char* e = std::getenv("MONC_PROJ_PIPE_EF");
+        p->pipe_ef = e && e[0] == '1';
+    }
+    if (p->pipe) p->nxp = (p->nxh + 15) & ~15;
+    p->smem_pipe = std::max((size_t)8 * std::max(1, 1024 / nx) * p->bs_row * csz, (size_t)p->tw_cols * p->bs_col * csz);
+
     // ---- workspace layout
     const size_t L = (size_t)nz * ny * p->nxp;
     size_t off = 0;
@@ -771,6 +892,9 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     p->off_sync = off;                                // tickets and per-level counters of the fused kernels
     p->sync_bytes = (size_t)(2 + 10 * nz) * sizeof(unsigned);
     off = align256(off + p->sync_bytes);
+    p->off_groups = off;                              // pipelines: per (level, line group) counters
+    p->groups_bytes = p->pipe ? (size_t)nz * (p->nxp / 16 + 1) * sizeof(unsigned) : 0;
+    off = align256(off + p->groups_bytes);
     p->refine_passes = std::min(4, env_int("MONC_PROJ_REFINE_PASSES", kRefinePasses));
     p->off_phipass = off;                             // refinement passes: one pass's potential (FP64)
     if (precision == MONC_PROJ_REFINED) off = align256(off + (size_t)nx * ny * nz * sizeof(double));
@@ -859,19 +983,48 @@ int monc_proj_plan(monc_proj_plan_t* out, int nx, int ny, int nz, double dx, dou
     TableOffsets to{};
     plan_prepare(p, nx, ny, nz, dx, dy, dz, rho_c, rho_f, precision, blob, to);
     cudaGetDevice(&p->device);
-    const int ar = plan_kernel_attrs(p);
-    if (ar != MONC_PROJ_OK) { delete p; return ar; }
 
+    // the tables' device memory, from the caller's allocator if one is set
     void* d = nullptr;
-    if (cudaMalloc(&d, blob.size()) != cudaSuccess) { cudaGetLastError(); delete p; return MONC_PROJ_ENOMEM; }
+    {
+        std::lock_guard<std::mutex> lock(g_alloc_mu);
+        if (g_alloc) {
+            d = g_alloc(blob.size(), g_alloc_user);
+            p->tables_free = g_free;
+            p->tables_user = g_alloc_user;
+        } else if (cudaMalloc(&d, blob.size()) != cudaSuccess) {
+            cudaGetLastError();
+            d = nullptr;
+        }
+    }
+    if (!d) { delete p; return MONC_PROJ_ENOMEM; }
+    p->dev_tables = d;
+    auto fail = [&](int rc) {
+        if (p->tables_free) p->tables_free(d, p->tables_user);
+        else cudaFree(d);
+        delete p;
+        return rc;
+    };
+    if ((uintptr_t)d & 255) return fail(MONC_PROJ_EINVAL);
+    const int ar = plan_kernel_attrs(p);
+    if (ar != MONC_PROJ_OK) return fail(ar);
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemcpyAsync(d, blob.data(), blob.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
-        cudaFree(d); delete p; return MONC_PROJ_ECUDA;
+        cudaGetLastError();
+        return fail(MONC_PROJ_ECUDA);
     }
-    p->dev_tables = d;
     plan_bind(p, (unsigned char*)d, to);
     *out = p;
+    return MONC_PROJ_OK;
+}
+
+int monc_proj_set_allocator(monc_proj_alloc_fn alloc, monc_proj_free_fn release, void* user) {
+    if ((alloc == nullptr) != (release == nullptr)) return MONC_PROJ_EINVAL;
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    g_alloc = alloc;
+    g_free = release;
+    g_alloc_user = alloc ? user : nullptr;
     return MONC_PROJ_OK;
 }
 
@@ -1101,7 +1254,8 @@ int monc_proj_destroy(monc_proj_plan_t plan) {
     cudaGetDevice(&dev);
     if (dev != plan->device) cudaSetDevice(plan->device);
     for (cudaEvent_t e : plan->prof_events) cudaEventDestroy(e);
-    cudaFree(plan->dev_tables);
+    if (plan->tables_free) plan->tables_free(plan->dev_tables, plan->tables_user);
+    else cudaFree(plan->dev_tables);
     if (dev != plan->device && dev >= 0) cudaSetDevice(dev);
     delete plan;
     return MONC_PROJ_OK;
@@ -1136,7 +1290,7 @@ int monc_proj_autotune(monc_proj_plan_t plan, const void* u, const void* v, cons
         if (col_threads) *col_threads = plan->col_threads;
         return rc;
     };
-    if (plan->fused || plan->persist_cols || plan->tma_cols || (!plan->ct_rows && !plan->ct_cols))
+    if (plan->fused || plan->persist_cols || plan->tma_cols || plan->pipe || (!plan->ct_rows && !plan->ct_cols))
         return report(MONC_PROJ_OK);
     if (reps <= 0) reps = 3;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1193,7 +1347,7 @@ int monc_proj_plan_info(monc_proj_plan_t plan, int* nx, int* ny, int* nz, int* p
     if (nx) *nx = plan->nx;
     if (ny) *ny = plan->ny;
     if (nz) *nz = plan->nz;
-    if (precision) *precision = plan->precision;
+    if (precision) *precision = plan->precision_api;
     const long long tot = (long long)plan->ny * plan->nxh;
     if (total_columns) *total_columns = tot;
     if (fp64_columns) *fp64_columns = plan->fp64_cols;
@@ -1210,24 +1364,15 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[MONC_PROJ_NOALL
 
 namespace {
 
-constexpr int kNoallocMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void* g_noalloc_base[kNoallocMaxDevices] = {};
-
-// Device address of the static array on the current device, looked up once
-// per device (with that device current).
+// Device address of the static array on the current device, looked up at
+// every call (cheap; nothing cached that a context reset could leave stale).
 int noalloc_base(void** out, int* device) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return MONC_PROJ_ECUDA; }
-    if (dev < 0 || dev >= kNoallocMaxDevices) return MONC_PROJ_EUNSUPPORTED;
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_base[dev]) {
-        void* ptr = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess || !ptr) { cudaGetLastError(); return MONC_PROJ_ECUDA; }
-        g_noalloc_base[dev] = ptr;
-    }
-    *out = g_noalloc_base[dev];
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) { cudaGetLastError(); return MONC_PROJ_ECUDA; }
+    *out = ptr;
     *device = dev;
     return MONC_PROJ_OK;
 }
@@ -1252,13 +1397,20 @@ extern "C" int monc_proj_solve_noalloc(int nx, int ny, int nz, double dx, double
     plan_prepare(&plan, nx, ny, nz, dx, dy, dz, rho_c, rho_f, precision, blob, to);
     const size_t tables = align256(blob.size());
     if (tables + plan.ws_bytes > (size_t)MONC_PROJ_NOALLOC_SCRATCH_BYTES) return MONC_PROJ_ESCRATCH;
+    // the table upload reads `blob`, which dies with this call: a graph
+    // captured here would replay a copy from freed host memory
+    cudaStream_t st = (cudaStream_t)stream;
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) { cudaGetLastError(); return MONC_PROJ_ECUDA; }
+        if (cs != cudaStreamCaptureStatusNone) return MONC_PROJ_EUNSUPPORTED;
+    }
 
     void* base = nullptr;
     const int br = noalloc_base(&base, &plan.device);
     if (br != MONC_PROJ_OK) return br;
     const int ar = plan_kernel_attrs(&plan);
     if (ar != MONC_PROJ_OK) return ar;
-    cudaStream_t st = (cudaStream_t)stream;
     // The blob carries a zeroed device error word, so every call starts clean.
     if (cudaMemcpyAsync(base, blob.data(), blob.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) {
         cudaGetLastError();

@@ -22,6 +22,11 @@ template <typename R> KernelFn pick_inv_cols_persist(int n);
 template <typename R> KernelFn pick_fwd_fused(int n);
 template <typename R> KernelFn pick_inv_fused(int n);
 template <typename R> KernelFn pick_tridiag();
+// FP32 persistent pipelines of the forward and inverse transforms (pipe.cuh);
+// nullptr for grids without them
+// (ef: the variants streaming u, v, w with evict-first L2 priority)
+KernelFn pick_fwd_pipe(int nx, int ny, bool ef = false);
+KernelFn pick_inv_pipe(int nx, int ny, bool ef = false);
 // refinement passes: FP32 transforms on FP64 fields (row kernels with F = double)
 KernelFn pick_refined_fwd_rows(int n);
 KernelFn pick_refined_inv_rows(int n);

@@ -35,9 +35,12 @@ MONC_PROJ_NOALLOC_SCRATCH_BYTES = 32 << 20
 MONC_PROJ_FP64 = 0
 MONC_PROJ_MIXED = 1
 MONC_PROJ_REFINED = 2
+MONC_PROJ_MIXED_Z64 = 3
 
-PRECISIONS = {"fp64": MONC_PROJ_FP64, "mixed": MONC_PROJ_MIXED, "refined": MONC_PROJ_REFINED}
-DTYPES = {MONC_PROJ_FP64: torch.float64, MONC_PROJ_MIXED: torch.float32, MONC_PROJ_REFINED: torch.float64}
+PRECISIONS = {"fp64": MONC_PROJ_FP64, "mixed": MONC_PROJ_MIXED, "refined": MONC_PROJ_REFINED,
+              "mixed_z64": MONC_PROJ_MIXED_Z64}
+DTYPES = {MONC_PROJ_FP64: torch.float64, MONC_PROJ_MIXED: torch.float32, MONC_PROJ_REFINED: torch.float64,
+          MONC_PROJ_MIXED_Z64: torch.float32}
 
 EXPORTS = [
     "monc_proj_plan", "monc_proj_workspace_size", "monc_proj_solve",
@@ -45,8 +48,12 @@ EXPORTS = [
     "monc_proj_destroy", "monc_proj_status_string", "monc_proj_plan_info",
     "monc_proj_profile", "monc_proj_profile_read", "monc_proj_phase_name",
     "monc_proj_solve_noalloc", "monc_proj_autotune", "monc_proj_host_staging_size", "monc_proj_solve_host",
-    "monc_proj_krylov_workspace_size", "monc_proj_solve_krylov",
+    "monc_proj_krylov_workspace_size", "monc_proj_solve_krylov", "monc_proj_set_allocator",
 ]
+
+# Allocator hooks of plan tables (monc_proj_set_allocator)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 
 class ProjError(RuntimeError):
@@ -97,6 +104,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.monc_proj_solve_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp, vp]
     L.monc_proj_krylov_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
     L.monc_proj_solve_krylov.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, d, i, i, ip, dp, vp]
+    L.monc_proj_set_allocator.argtypes = [ALLOC_FN, FREE_FN, vp]
     for name in EXPORTS:
         if name not in ("monc_proj_status_string", "monc_proj_phase_name"):
             getattr(L, name).restype = ctypes.c_int
@@ -283,6 +291,26 @@ def monc_proj_solve_noalloc(nx, ny, nz, dx, dy, dz, rho_c, rho_f, precision, u, 
         ptr(u), ptr(v), ptr(w), ptr(u_out), ptr(v_out), ptr(w_out), ptr(phi_out),
         ctypes.c_void_p(_stream_handle(stream)))
     _check(rc, "monc_proj_solve_noalloc")
+
+
+_allocator_refs = None
+
+
+def monc_proj_set_allocator(alloc=None, release=None):
+    """Install Python callables alloc(bytes) -> device pointer (int, 0 on
+    failure) and release(ptr) as the allocator of plan tables; no arguments
+    restore cudaMalloc / cudaFree.  The callbacks are kept alive here."""
+    global _allocator_refs
+    if alloc is None and release is None:
+        rc = load_library().monc_proj_set_allocator(ALLOC_FN(), FREE_FN(), None)
+        _allocator_refs = None
+        _check(rc, "monc_proj_set_allocator")
+        return
+    a = ALLOC_FN(lambda n, user: int(alloc(int(n)) or 0))
+    r = FREE_FN(lambda ptr, user: release(int(ptr or 0)))
+    rc = load_library().monc_proj_set_allocator(a, r, None)
+    _check(rc, "monc_proj_set_allocator")
+    _allocator_refs = (a, r)
 
 
 # ----------------------------------------------------------------- convenience

@@ -22,13 +22,13 @@ from paper_2009_12849_gb300 import workloads as W
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--grid", default="512,512,64")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "refined"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "refined", "mixed_z64"])
     ap.add_argument("--solves", type=int, default=3)
     ap.add_argument("--krylov", type=int, default=0, help="BiCGStab iterations per solve (0: FFT solve)")
     a = ap.parse_args()
     nx, ny, nz = (int(x) for x in a.grid.split(","))
     g = W.make_grid(nx, ny, nz, 10.0, 10.0, W.geometric_dz(nz, 5.0, 50.0))
-    dt = torch.float32 if a.precision == "mixed" else torch.float64
+    dt = torch.float32 if a.precision in ("mixed", "mixed_z64") else torch.float64
     dev = torch.device("cuda", 0)
     u, v, w = (torch.from_numpy(x).to(dev, dt) for x in W.random_fields_f32(g, 2, True))
     P = MP.Projector.from_grid(g, a.precision, dev)

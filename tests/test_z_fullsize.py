@@ -15,43 +15,7 @@ import torch
 
 import oracle as O
 from paper_2009_12849_gb300 import workloads as W
-
-
-def sampled_modes(g, extra=10, seed=7):
-    rng = np.random.default_rng(seed)
-    nxh = g.nx // 2 + 1
-    kx = np.concatenate([[0, 1, 0, 1, 2, nxh - 1], rng.integers(0, nxh, extra)])
-    ky = np.concatenate([[0, 0, 1, g.ny - 1, 3, g.ny // 2], rng.integers(0, g.ny, extra)])
-    return kx, ky
-
-
-def sampled_mode_error(g, u, v, w, outs, kx, ky):
-    """Relative L2 error of the outputs' DFTs at (kx, ky) against the oracle."""
-    ref = O.project_modes(u, v, w, g.dx, g.dy, g.dz, g.rho_c, g.rho_f, kx, ky)
-    num = den = 0.0
-    for name, arr in zip(("u", "v", "w"), outs):
-        got = O.mode_dft(arr, kx, ky)
-        num += float(np.sum(np.abs(got - ref[name]) ** 2))
-        den += float(np.sum(np.abs(ref[name]) ** 2))
-    return (num / den) ** 0.5
-
-
-def divergence_residual_levels(g, u, v, w, outs):
-    """||D(out)|| / ||D(in)|| over all cells, one level at a time (FP64)."""
-    dn = dd = 0.0
-    zero = np.zeros((g.ny, g.nx))
-    for k in range(g.nz):
-        for fields, is_out in ((outs, True), ((u, v, w), False)):
-            fu, fv, fw = fields
-            lo = np.asarray(fw[k], np.float64) if k > 0 else zero
-            hi = np.asarray(fw[k + 1], np.float64) if k < g.nz - 1 else zero
-            d = O.divergence_level(np.asarray(fu[k], np.float64), np.asarray(fv[k], np.float64), lo, hi,
-                                   g.dx, g.dy, g.dz[k], g.rho_c[k], g.rho_f[k], g.rho_f[k + 1])
-            if is_out:
-                dn += float(np.sum(d * d))
-            else:
-                dd += float(np.sum(d * d))
-    return (dn / dd) ** 0.5
+from tests.oracle_checks import divergence_residual_levels, sampled_mode_error, sampled_modes
 
 
 def test_checker_against_the_full_oracle():
@@ -69,14 +33,15 @@ def test_checker_against_the_full_oracle():
 
 
 @pytest.mark.gpu
-def test_1024x256_mixed_sampled_modes_and_divergence():
+@pytest.mark.parametrize("prec", ["mixed", "mixed_z64"])
+def test_1024x256_mixed_sampled_modes_and_divergence(prec):
     import __graft_entry__ as ge
     ge.build()
     from paper_2009_12849_gb300 import monc_proj as mp
     g, seed, mode = W.workload_1024()
     u_h, v_h, w_h = W.random_fields_f32(g, seed, mode)
     dev = torch.device("cuda", 0)
-    P = mp.Projector.from_grid(g, "mixed", dev)
+    P = mp.Projector.from_grid(g, prec, dev)
     u, v, w = (torch.from_numpy(a).to(dev) for a in (u_h, v_h, w_h))
     out = (torch.empty_like(u), torch.empty_like(v), torch.empty_like(w))
     P.solve(u, v, w, out=out)
@@ -88,7 +53,7 @@ def test_1024x256_mixed_sampled_modes_and_divergence():
     kx, ky = sampled_modes(g)
     err = sampled_mode_error(g, u_h, v_h, w_h, outs, kx, ky)
     div = divergence_residual_levels(g, u_h, v_h, w_h, outs)
-    print(f"1024x1024x256 mixed: rel err {err:.3e} at {len(kx)} modes, divergence residual {div:.3e}")
+    print(f"1024x1024x256 {prec}: rel err {err:.3e} at {len(kx)} modes, divergence residual {div:.3e}")
     assert err < 1e-5
     assert div < 1e-6
     assert np.all(outs[2][0] == 0) and np.all(outs[2][-1] == 0)
