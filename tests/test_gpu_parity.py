@@ -15,7 +15,7 @@ from paper_2009_12849_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "mixed": 1e-5, "refined": 1e-11}
+TOL = {"fp64": 1e-12, "mixed": 1e-5, "refined": 1e-12}
 DIV_TOL = {"fp64": 1e-10, "mixed": 1e-6, "refined": 1e-10}
 
 
