@@ -474,6 +474,39 @@ def main():
         PZ.close()
         del oz
 
+    # ---- the forward column transforms on the tensor cores (split TF32 x 3
+    # and BF16 x 6, opt-in): time and accuracy of the whole mixed solve
+    tensor_cols = None
+    if not args.no_fp64:
+        tensor_cols = {}
+        for fmt, name in ((1, "tf32x3"), (2, "bf16x6")):
+            os.environ["MONC_PROJ_TC"] = str(fmt)
+            PT = MP.Projector.from_grid(g, "mixed", dev)
+            os.environ.pop("MONC_PROJ_TC", None)
+            ot = (torch.empty_like(u), torch.empty_like(v), torch.empty_like(w))
+            for _ in range(2):
+                PT.solve(u, v, w, out=ot)
+            torch.cuda.synchronize(dev)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            MP.monc_proj_profile(PT.plan, True)
+            a0.record(stream)
+            for _ in range(5):
+                PT.solve(u, v, w, out=ot)
+            a1.record(stream)
+            torch.cuda.synchronize(dev)
+            MP.monc_proj_profile(PT.plan, False)
+            pt = MP.monc_proj_profile_read(PT.plan)
+            mst = a0.elapsed_time(a1) / 5
+            leg = {"ms_per_step": mst, "value": npts / (mst * 1e-3) / 1e6, "unit": UNIT,
+                   "fwd_cols_tc_ms": pt["phases"].get("fwd_cols_tc", 0.0) / max(pt["solves"], 1),
+                   "device_status": PT.sync_status()}
+            if not args.no_check and rank == 0:
+                leg["accuracy"] = verify(g, (u, v, w), ot, o64)
+            tensor_cols[name] = leg
+            PT.close()
+            del ot
+
     # ---- refinement: mixed passes on FP64 fields (FP64-level accuracy)
     refined = None
     if not args.no_fp64 and not args.no_refined:
@@ -583,6 +616,7 @@ def main():
         "gpu_launches": nsolves * len(phases),
         "fp64_path": fp64,
         "a3_variants": a3_variants,
+        "tensor_core_columns": tensor_cols,
         "refined_path": refined,
         "configs": configs,
         "link": link,

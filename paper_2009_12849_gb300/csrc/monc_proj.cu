@@ -61,6 +61,8 @@ struct monc_proj_plan_s {
     int bs_row, bs_col;
     size_t smem_fwd_rows, smem_cols, smem_fcols, smem_inv_rows[2];
     bool pipe;                            // persistent pipelines of the transforms (pipe.cuh), opt-in
+    int tc_cols;                          // tensor-core split-precision forward columns (tcdft.cuh), opt-in:
+                                          // 0 off, 1 TF32 x 3, 2 BF16 x 6
     long long spin_limit;                 // polls before a bounded dependency wait gives up
     monc_proj_free_fn tables_free;        // how dev_tables is released (NULL: cudaFree)
     void* tables_user;
@@ -81,9 +83,9 @@ struct monc_proj_plan_s {
 
 namespace {
 
-constexpr int kPhases = 9;
+constexpr int kPhases = 10;
 const char* const kPhaseNames[kPhases] = {"fwd_rows", "fwd_cols", "tridiag", "inv_cols", "inv_rows",
-                                          "fwd_fused", "inv_fused", "fwd_pipe", "inv_pipe"};
+                                          "fwd_fused", "inv_fused", "fwd_pipe", "inv_pipe", "fwd_cols_tc"};
 
 // Start/end events of every phase of one recorded solve (null when not recording).
 struct PhaseMarks {
@@ -475,10 +477,17 @@ int launch_solve(monc_proj_plan_s* p, const ProjParams& q, cudaStream_t st) {
         pm.start(0, st);
         ks.fwd_rows<<<nz * p->nrb_fwd, p->thr_fwd_rows, p->smem_fwd_rows, st>>>(q);
         pm.end(0, st);
-        pm.start(1, st);
-        if (!(p->tma_cols && launch_cols_tma<R>(p, q, false, st)))
+        const int fc_phase = (p->tc_cols && sizeof(R) == 4) ? 9 : 1;
+        pm.start(fc_phase, st);
+        if (fc_phase == 9) {
+            // the tensor-core kernel's own tiles of 8 columns
+            ProjParams qt = q;
+            qt.ntiles = (p->nxh + 7) / 8;
+            pick_fwd_cols_tc(p->ny, p->tc_cols)<<<nz * qt.ntiles, 256, fwd_cols_tc_smem(p->tc_cols), st>>>(qt);
+        } else if (!(p->tma_cols && launch_cols_tma<R>(p, q, false, st))) {
             ks.fwd_cols<<<n_fcols, p->thr_cols, p->smem_fcols, st>>>(q);
-        pm.end(1, st);
+        }
+        pm.end(fc_phase, st);
         pm.start(2, st);
         pick_tridiag<R>()<<<(unsigned)((ncol + kTriThreads - 1) / kTriThreads), kTriThreads, 0, st>>>(q);
         pm.end(2, st);
@@ -627,6 +636,12 @@ int setup_pipe(monc_proj_plan_s* p) {
 int plan_kernel_attrs(monc_proj_plan_s* p) {
     const int r = p->precision == MONC_PROJ_FP64 ? set_kernel_attrs<double>(p) : set_kernel_attrs<float>(p);
     if (r != MONC_PROJ_OK) return r;
+    if (p->tc_cols && cudaFuncSetAttribute((const void*)pick_fwd_cols_tc(p->ny, p->tc_cols),
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)fwd_cols_tc_smem(p->tc_cols)) != cudaSuccess) {
+        cudaGetLastError();
+        p->tc_cols = 0;
+    }
     if (p->pipe) {
         const int rp = setup_pipe(p);
         if (rp != MONC_PROJ_OK) return rp;
@@ -875,6 +890,14 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
         p->pipe_ef = e && e[0] == '1';
     }
     if (p->pipe) p->nxp = (p->nxh + 15) & ~15;
+    // tensor-core split-precision forward columns: MONC_PROJ_TC=1 (TF32 x 3) or
+    // 2 (BF16 x 6), mixed plans with ny = 1024 (read when the plan is made)
+    {
+        const char* e = std::getenv("MONC_PROJ_TC");
+        const int fmt = (e && (e[0] == '1' || e[0] == '2')) ? e[0] - '0' : 0;
+        p->tc_cols = (fmt && precision == MONC_PROJ_MIXED && cty && pick_fwd_cols_tc(ny, fmt) && !p->pipe &&
+                      !p->fused && !p->tma_cols) ? fmt : 0;
+    }
     p->smem_pipe = std::max((size_t)8 * std::max(1, 1024 / nx) * p->bs_row * csz, (size_t)p->tw_cols * p->bs_col * csz);
 
     // ---- workspace layout

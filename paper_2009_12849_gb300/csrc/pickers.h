@@ -27,6 +27,11 @@ template <typename R> KernelFn pick_tridiag();
 // (ef: the variants streaming u, v, w with evict-first L2 priority)
 KernelFn pick_fwd_pipe(int nx, int ny, bool ef = false);
 KernelFn pick_inv_pipe(int nx, int ny, bool ef = false);
+// tensor-core split-precision forward column transforms (tcdft.cuh), format
+// 1 (TF32 x 3) or 2 (BF16 x 6): nullptr unless ny = 1024; and their dynamic
+// shared memory
+KernelFn pick_fwd_cols_tc(int ny, int fmt);
+unsigned fwd_cols_tc_smem(int fmt);
 // refinement passes: FP32 transforms on FP64 fields (row kernels with F = double)
 KernelFn pick_refined_fwd_rows(int n);
 KernelFn pick_refined_inv_rows(int n);
