@@ -252,6 +252,92 @@ int monc_proj_profile_read(monc_proj_plan_t plan, int max_phases, double* total_
 /* Static name of a kernel phase ("fwd_rows", "tridiag", ...), NULL if out of range. */
 const char* monc_proj_phase_name(int phase);
 
+/* ---------------------------------------------------------------------------
+ * Phases of a distributed projection (paper, Section 4: the model's FFT
+ * solver decomposes the domain into pencils and moves data between them with
+ * a global all-to-all for every transform).  One large projection sharded
+ * over P processes runs, per process:
+ *   1. monc_proj_forward_slab   on its z-slab of levels [k0, k1): the
+ *      divergence and the forward horizontal transform (steps a1-a2);
+ *   2. an all-to-all (the caller's collective) that turns the slabs of the
+ *      spectrum into pencils of spectral rows [j0, j1) over all levels;
+ *   3. monc_proj_vertical_pencil on its pencil: the vertical solve (a3),
+ *      giving p^ and the vertical gradient gz^;
+ *   4. the reverse all-to-all of p^ and gz^ back to z-slabs;
+ *   5. monc_proj_inverse_slab   on its slab: the inverse transforms and the
+ *      correction of u, v, w (a4-a5).
+ * Each call runs the kernels of monc_proj_solve on its sub-domain, so the
+ * slab and pencil results are those of the whole solve (bitwise, for the
+ * same plan).  The plan is made for the whole grid (nx, ny, nz and the whole
+ * column's profiles); only FP64 and mixed plans with the default kernels are
+ * accepted (EUNSUPPORTED otherwise).  All arrays are device arrays of the
+ * plan's element type; spectra are complex (two reals per value).
+ * Pointers must be 16-byte aligned, the workspace 256-byte aligned and at
+ * least monc_proj_workspace_size() bytes; the calls enqueue on `stream` and
+ * return without waiting.  Errors: EINVAL for a NULL pointer, a misaligned
+ * pointer or an empty or out-of-range slab or pencil.
+ * ------------------------------------------------------------------------- */
+
+/* Row pitch (complex values) of the spectral arrays: rows hold the kx =
+ * 0 .. nx/2 half spectrum and are padded to `*nxp` values. */
+int monc_proj_spectral_pitch(monc_proj_plan_t plan, int* nxp);
+
+/*
+ * a1-a2 on the cell levels k0 .. k1-1 (0 <= k0 < k1 <= nz).
+ *   u, v   [k1-k0][ny][nx]     the slab's levels of u and v
+ *   w      [k1-k0+1][ny][nx]   the slab's faces k0 .. k1 (face k1 is read
+ *                              only when k1 < nz; face 0 is never read)
+ *   dhat   [k1-k0][ny][nxp]    out: the horizontal spectrum (unnormalised
+ *                              forward transform) of rho_c[k] dz[k] D[k], D
+ *                              the divergence of step a1 at level k
+ */
+int monc_proj_forward_slab(monc_proj_plan_t plan, int k0, int k1, const void* u, const void* v, const void* w,
+                           void* dhat, void* workspace, void* stream);
+
+/*
+ * a3 on the spectral rows j0 .. j1-1 (0 <= j0 < j1 <= ny; row j holds
+ * wavenumber ky = j for j <= ny/2 and j - ny above) of every level.
+ *   spec   [nz][j1-j0][nxp]    in: D^ of the pencil's rows; out: p^
+ *   gz     [nz][j1-j0][nxp]    out: the vertical gradient gz^ at faces
+ *                              1 .. nz-1 (level 0 holds scratch)
+ * p^ and gz^ carry the inverse transform's 1/(nx ny), so step a4 is an
+ * unnormalised inverse transform.
+ * The mean mode (kx = ky = 0) carries the potential's pin (level 0 zero);
+ * in a mixed plan the rows of small |lambda| run FP64 as in the whole solve.
+ */
+int monc_proj_vertical_pencil(monc_proj_plan_t plan, int j0, int j1, void* spec, void* gz, void* workspace,
+                              void* stream);
+
+/*
+ * a4-a5 on the cell levels k0 .. k1-1.
+ *   phat, gz   [k1-k0][ny][nxp]    p^ and gz^ of the slab's levels (gz^ of
+ *                                  level 0 is not read)
+ *   u, v       [k1-k0][ny][nx]     the provisional velocities of the slab
+ *   w          [k1-k0+1][ny][nx]   faces k0 .. k1 (face k1 is not read)
+ *   u_out, v_out [k1-k0][ny][nx], w_out [k1-k0+1][ny][nx]: the projected
+ *              fields; faces k0 .. k1-1 of w_out are written, and face k1
+ *              (zero) only when k1 == nz; the outputs may alias the inputs
+ */
+int monc_proj_inverse_slab(monc_proj_plan_t plan, int k0, int k1, const void* phat, const void* gz, const void* u,
+                           const void* v, const void* w, void* u_out, void* v_out, void* w_out, void* workspace,
+                           void* stream);
+
+/*
+ * Reordering for the all-to-alls.  Items (levels or spectral rows) are split
+ * over `parts` processes in contiguous blocks: with n = q*parts + r, part s
+ * holds [s*q + min(s, r), (s+1)*q + min(s+1, r)) (the first r parts one item
+ * more).  Pack turns a slab [nzl][ny][nxp] (complex) into the blocks for
+ * parts 0 .. parts-1, one after the other, block s [nzl][rows of s][nxp]:
+ * the send buffer of the slab -> pencil all-to-all, whose receive buffer,
+ * the blocks of slabs 0 .. parts-1 one after the other, is the pencil
+ * [nz][rows][nxp] itself.  Unpack is the inverse map, for the pencil -> slab
+ * all-to-all (whose send buffer is the pencil itself: the levels of slab s
+ * are one block).  1 <= nzl <= nz; src and dst must not overlap.
+ */
+int monc_proj_pack_pencils(monc_proj_plan_t plan, int nzl, int parts, const void* slab, void* packed, void* stream);
+int monc_proj_unpack_pencils(monc_proj_plan_t plan, int nzl, int parts, const void* packed, void* slab,
+                             void* stream);
+
 /*
  * monc_proj_solve_noalloc -- one projection that allocates no device memory.
  *

@@ -62,6 +62,12 @@ struct ProjParams {
     int bs_col;                 // smem stride of a column transform
     HandoffArgs ho;             // hand-off of intermediates in L2 (pipelines); zero: none
     long long spin_limit;       // polls before a bounded dependency wait gives up (timeout bit)
+    // sub-domains of a distributed solve (the pencil decomposition): arrays
+    // hold levels kbase .. kbase + nz - 1 of a column of nz_glob levels (the
+    // plan's tables and the top and bottom boundaries are global), and the
+    // vertical solve's spectral rows are ky_base .. ky_base + ny - 1.  A whole
+    // solve has kbase = ky_base = 0 and nz_glob = nz.
+    int kbase, nz_glob, ky_base;
 };
 
 template <typename R> __device__ __forceinline__ const cplx<R>* ctab(const void* p) { return (const cplx<R>*)p; }
@@ -121,9 +127,11 @@ __device__ __forceinline__ void fwd_rows_task(const ProjParams& p, unsigned char
     // per-level coefficients in the field precision (FP32 fields read the
     // FP32 tables: no FP64 conversions in the kernel)
     constexpr bool f32 = sizeof(F) == 4;
-    const F sv = f32 ? (F)p.svol32[k] : (F)p.svol[k];
-    const F rlo = f32 ? (F)p.rflo32[k] : (F)p.rflo[k];
-    const F rhi = f32 ? (F)p.rfhi32[k] : (F)p.rfhi[k];
+    const int kg = p.kbase + k;                 // global level: tables and boundaries
+    const bool below = kg > 0, above = kg < p.nz_glob - 1;
+    const F sv = f32 ? (F)p.svol32[kg] : (F)p.svol[kg];
+    const F rlo = f32 ? (F)p.rflo32[kg] : (F)p.rflo[kg];
+    const F rhi = f32 ? (F)p.rfhi32[kg] : (F)p.rfhi[kg];
     const F idx = f32 ? (F)p.idx32 : (F)p.idx, idy = f32 ? (F)p.idy32 : (F)p.idy;
 
     const C* res;
@@ -165,8 +173,8 @@ __device__ __forceinline__ void fwd_rows_task(const ProjParams& p, unsigned char
                         um1[c] = i0 == 0 ? ld1(row + NX - 1, u) : u[row + i0 - 1];
                         v4[c] = ld4(row + i0, v);
                         vm4[c] = ld4(rowm + i0, v);
-                        if (k > 0) wl4[c] = ld4(row + i0, w);
-                        if (k < nz - 1) wh4[c] = ld4(row + plane + i0, w);
+                        if (below) wl4[c] = ld4(row + i0, w);
+                        if (above) wh4[c] = ld4(row + plane + i0, w);
                     }
                 }
             }
@@ -216,8 +224,8 @@ __device__ __forceinline__ void fwd_rows_task(const ProjParams& p, unsigned char
                         um[c] = u[row + im];
                         vc[c] = v[row + i];
                         vm[c] = v[rowm + i];
-                        if (k > 0) wl[c] = w[row + i];
-                        if (k < nz - 1) wh[c] = w[row + plane + i];
+                        if (below) wl[c] = w[row + i];
+                        if (above) wh[c] = w[row + plane + i];
                     }
                 }
             }
@@ -678,16 +686,17 @@ __global__ void __launch_bounds__(kTriThreads, 1024 / kTriThreads) k_tridiag(Pro
     const int r = (int)(col / nxw);
     const int kx = (int)(col - (long long)r * nxw);
     if (r >= p.ny || kx >= p.nxh) return;
-    const int ky = (r & 1) ? p.ny - 1 - (r >> 1) : (r >> 1);
+    const int ky = (r & 1) ? p.ny - 1 - (r >> 1) : (r >> 1);      // local spectral row
+    const int kyg = p.ky_base + ky;                                 // global wavenumber row
     const size_t base = (size_t)ky * p.nxp + kx;
-    const double lam = p.lamx[kx] + p.lamy[ky];
-    const bool mean = (kx == 0 && ky == 0);
+    const double lam = p.lamx[kx] + p.lamy[kyg];
+    const bool mean = (kx == 0 && kyg == 0);
     if (sizeof(R) == 8) {
         tridiag_column_inplace<double>(p, base, lam, mean);
     } else {
-        const double lam_warp = p.lamx[kx & ~31] + p.lamy[ky];   // smallest |lambda| of the warp
+        const double lam_warp = p.lamx[kx & ~31] + p.lamy[kyg];  // smallest |lambda| of the warp
         // the warp holding the mean column always runs FP64 (it carries the pin)
-        if (-lam_warp < p.lam_fp64 || (ky == 0 && kx < 32)) tridiag_column_mixed64(p, base, lam, mean);
+        if (-lam_warp < p.lam_fp64 || (kyg == 0 && kx < 32)) tridiag_column_mixed64(p, base, lam, mean);
         else if (p.nz <= kTriSeg * kTriMaxSeg) tridiag_column_ckpt32(p, base, (float)lam);
         else tridiag_column_inplace<float>(p, base, (float)lam, mean);
     }
@@ -716,7 +725,7 @@ __device__ __forceinline__ InvColField<R> inv_col_field(const ProjParams& p, int
     r.dst = (f == 0) ? (C*)p.Tp : (f == 1) ? (C*)p.Tgy : (f == 2) ? (C*)p.Tgz : (C*)p.Tphi;
     r.ey = (f == 1) ? ctab<R>(p.ey) : nullptr;
     r.ex = (f == 0);
-    r.skip = (f == 2 && k == 0);
+    r.skip = (f == 2 && p.kbase + k == 0);
     return r;
 }
 
@@ -769,7 +778,7 @@ __device__ __forceinline__ void inv_cols_tile(const ProjParams& p, unsigned char
             __syncthreads();
             inv_cols_ct_task<R, NY>(p, k, kx0, 3, buf);
         }
-    } else if (k > 0) {
+    } else if (p.kbase + k > 0) {
         inv_cols_ct_task<R, NY>(p, k, kx0, 2, buf);
     }
 }
@@ -841,7 +850,7 @@ __device__ __forceinline__ cplx<R> hermitian_at(const cplx<R>* row, int nx, int 
 
 template <typename R>
 __device__ __forceinline__ cplx<R> inv_spectrum(const ProjParams& p, int k, int j, int ch, int kx) {
-    if (j >= p.ny || (ch == 2 && k == 0)) return cmk<R>((R)0, (R)0);
+    if (j >= p.ny || (ch == 2 && p.kbase + k == 0)) return cmk<R>((R)0, (R)0);
     const cplx<R>* row = inv_channel_spectrum<R>(p, ch) + ((size_t)k * p.ny + j) * p.nxp;
     return hermitian_at<R>(row, p.nx, p.nxh, kx);
 }
@@ -863,13 +872,15 @@ __device__ __forceinline__ void inv_rows_ct(const ProjParams& p, unsigned char* 
     constexpr int NXH = NX / 2 + 1;
     const int npr = rows / 2;                    // transforms (row pairs) per task
     F* out = (ch == 0) ? (F*)p.uo : (ch == 1) ? (F*)p.vo : (ch == 2) ? (F*)p.wo : (F*)p.phi;
-    if (ch == 2 && k == 0) {
+    const int kg = p.kbase + k;                   // global level (boundaries)
+    const bool top = kg == p.nz_glob - 1;
+    if (ch == 2 && kg == 0) {
         // bottom face: w = 0
         for (int t = Sc::tid(); t < rows * NX; t += Sc::size()) {
             const int j = j0 + t / NX;
             if (j < ny) {
                 out[(size_t)j * NX + (t % NX)] = (F)0;
-                if (nz == 1) out[plane + (size_t)j * NX + (t % NX)] = (F)0;   // top face too
+                if (top) out[plane + (size_t)j * NX + (t % NX)] = (F)0;   // top face too
             }
         }
         return;
@@ -936,7 +947,7 @@ __device__ __forceinline__ void inv_rows_ct(const ProjParams& p, unsigned char* 
                     const F res = (ch < 3) ? prev[i][h][r] - val : (upd ? prev[i][h][r] + val : val);
                     if constexpr (ef) st_ef((float*)&out[row + r * ns], res, pol);
                     else out[row + r * ns] = res;
-                    if (ch == 2 && k == nz - 1) out[row + r * ns + plane] = (F)0;
+                    if (ch == 2 && top) out[row + r * ns + plane] = (F)0;
                 }
             }
         };
@@ -957,7 +968,7 @@ __device__ __forceinline__ void inv_rows_ct(const ProjParams& p, unsigned char* 
                 for (int r = 0; r < LRAD; ++r) {
                     const F val = (F)(h ? x[r].y : x[r].x);
                     out[row + r * ns] = (ch < 3) ? prev[r] - val : (upd ? prev[r] + val : val);
-                    if (ch == 2 && k == nz - 1) out[row + r * ns + plane] = (F)0;
+                    if (ch == 2 && top) out[row + r * ns + plane] = (F)0;
                 }
             }
         };
@@ -1042,7 +1053,7 @@ __global__ void __launch_bounds__(512) k_inv_rows(ProjParams p) {
                         const size_t o = (size_t)k * plane + (size_t)j * nx + i;
                         uu[c] = u[o];
                         vv[c] = v[o];
-                        if (k > 0) ww[c] = w[o];
+                        if (p.kbase + k > 0) ww[c] = w[o];
                     }
                 }
             }
@@ -1070,8 +1081,8 @@ __global__ void __launch_bounds__(512) k_inv_rows(ProjParams p) {
                 }
                 uo[o] = uu[c] - val[0];
                 vo[o] = vv[c] - val[1];
-                wo[o] = (k == 0) ? (F)0 : (F)(ww[c] - val[2]);
-                if (k == nz - 1) wo[o + plane] = (F)0;
+                wo[o] = (p.kbase + k == 0) ? (F)0 : (F)(ww[c] - val[2]);
+                if (p.kbase + k == p.nz_glob - 1) wo[o + plane] = (F)0;
                 if (nch == 4) ph[o] = val[3];
             }
         }

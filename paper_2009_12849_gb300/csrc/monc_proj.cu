@@ -323,6 +323,9 @@ ProjParams make_params(const monc_proj_plan_s* p, const void* u, const void* v, 
     q.bs_row = p->bs_row; q.bs_col = p->bs_col;
     q.nch = phi ? 4 : 3;
     q.spin_limit = p->spin_limit;
+    q.kbase = 0;
+    q.nz_glob = p->nz;
+    q.ky_base = 0;
     q.rows_inv = p->rows_inv[q.nch == 4 ? 1 : 0];
     q.nrb_inv = (p->ny + q.rows_inv - 1) / q.rows_inv;
     return q;
@@ -1068,6 +1071,158 @@ int monc_proj_solve(monc_proj_plan_t plan, const void* u, const void* v, const v
     ProjParams q = make_params(plan, u, v, w, u_out, v_out, w_out, phi_out, workspace);
     cudaStream_t st = (cudaStream_t)stream;
     return run_solve(plan, q, st);
+}
+
+// ---------------------------------------------------------------------------
+// Phases of a distributed solve (the pencil decomposition): the forward
+// transform of a slab of levels, the vertical solve of a pencil of spectral
+// rows, the inverse transform of a slab.  They run the kernels of the whole
+// solve on sub-domains (ProjParams.kbase / nz_glob / ky_base).
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace mp {
+// Reordering of spectral rows between a z-slab and the blocks sent to the
+// pencils of a distributed solve.  slab: [nzl][ny][row]; packed: the blocks
+// of parts s = 0 .. parts-1 one after the other, block s [nzl][rows of s][row],
+// where part s holds the rows [s*q + min(s, r), ...) of ny = q*parts + r (the
+// first r parts one row more).  A row is `units` 16-byte words.  One block
+// per slab row; dir 0 copies slab -> packed, dir 1 packed -> slab.
+__global__ void __launch_bounds__(128) k_pencil_pack(const float4* __restrict__ src, float4* __restrict__ dst,
+                                                     int ny, int nzl, int parts, int units, int dir) {
+    const int row = blockIdx.x;                 // k * ny + j
+    const int k = row / ny, j = row - k * ny;
+    const int q = ny / parts, r = ny - q * parts;
+    int j0, nys;
+    if (j < r * (q + 1)) {
+        j0 = (j / (q + 1)) * (q + 1);
+        nys = q + 1;
+    } else {
+        j0 = r * (q + 1) + ((j - r * (q + 1)) / q) * q;
+        nys = q;
+    }
+    const size_t poff = ((size_t)nzl * j0 + (size_t)k * nys + (j - j0)) * units;
+    const size_t soff = (size_t)row * units;
+    const float4* a = src + (dir ? poff : soff);
+    float4* b = dst + (dir ? soff : poff);
+    for (int i = threadIdx.x; i < units; i += blockDim.x) b[i] = a[i];
+}
+}  // namespace mp
+
+namespace {
+size_t spec_elem(const monc_proj_plan_s* p) { return p->precision == MONC_PROJ_FP64 ? 16 : 8; }
+
+template <typename R>
+int launch_forward_slab(monc_proj_plan_s* p, const ProjParams& q, cudaStream_t st) {
+    const SolveKernels ks = pick_kernels<R>(p);
+    const int nzl = q.nz;
+    ks.fwd_rows<<<nzl * p->nrb_fwd, p->thr_fwd_rows, p->smem_fwd_rows, st>>>(q);
+    ks.fwd_cols<<<nzl * p->ntiles, p->thr_cols, p->smem_fcols, st>>>(q);
+    return cudaGetLastError() == cudaSuccess ? MONC_PROJ_OK : MONC_PROJ_ECUDA;
+}
+
+template <typename R>
+int launch_inverse_slab(monc_proj_plan_s* p, const ProjParams& q, cudaStream_t st) {
+    const SolveKernels ks = pick_kernels<R>(p);
+    const int nzl = q.nz;
+    const int n_icols = nzl * p->ntiles * (p->ct_cols ? 2 : q.nch);
+    const int n_irows = nzl * q.nrb_inv * (p->ct_rows ? q.nch : 1);
+    ks.inv_cols<<<n_icols, p->thr_cols, p->smem_cols, st>>>(q);
+    ks.inv_rows<<<n_irows, p->thr_inv_rows[0], p->smem_inv_rows[0], st>>>(q);
+    return cudaGetLastError() == cudaSuccess ? MONC_PROJ_OK : MONC_PROJ_ECUDA;
+}
+
+// The kernels of the opt-in variants (fused, persistent, pipelined) and the
+// refinement passes are not sub-domain aware; slab phases run the default
+// kernels of FP64 and mixed plans.
+bool slab_plan_ok(const monc_proj_plan_s* p) {
+    return (p->precision == MONC_PROJ_FP64 || p->precision == MONC_PROJ_MIXED) && !p->fused && !p->persist_cols &&
+           !p->pipe;
+}
+}  // namespace
+
+extern "C" {
+
+int monc_proj_spectral_pitch(monc_proj_plan_t plan, int* nxp) {
+    if (!plan || !nxp) return MONC_PROJ_EINVAL;
+    *nxp = plan->nxp;
+    return MONC_PROJ_OK;
+}
+
+int monc_proj_forward_slab(monc_proj_plan_t plan, int k0, int k1, const void* u, const void* v, const void* w,
+                           void* dhat, void* workspace, void* stream) {
+    if (!plan || !u || !v || !w || !dhat || !workspace) return MONC_PROJ_EINVAL;
+    if (k0 < 0 || k1 <= k0 || k1 > plan->nz) return MONC_PROJ_EINVAL;
+    if (!slab_plan_ok(plan)) return MONC_PROJ_EUNSUPPORTED;
+    const void* ptrs[] = {u, v, w, dhat};
+    for (const void* x : ptrs)
+        if (((uintptr_t)x) & 15) return MONC_PROJ_EINVAL;
+    if (((uintptr_t)workspace) & 255) return MONC_PROJ_EINVAL;
+    ProjParams q = make_params(plan, u, v, w, nullptr, nullptr, nullptr, nullptr, workspace);
+    q.nz = k1 - k0;
+    q.kbase = k0;
+    q.S = dhat;
+    cudaStream_t st = (cudaStream_t)stream;
+    return plan->precision == MONC_PROJ_FP64 ? launch_forward_slab<double>(plan, q, st)
+                                             : launch_forward_slab<float>(plan, q, st);
+}
+
+int monc_proj_vertical_pencil(monc_proj_plan_t plan, int j0, int j1, void* spec, void* gz, void* workspace,
+                              void* stream) {
+    if (!plan || !spec || !gz || !workspace) return MONC_PROJ_EINVAL;
+    if (j0 < 0 || j1 <= j0 || j1 > plan->ny) return MONC_PROJ_EINVAL;
+    if (!slab_plan_ok(plan)) return MONC_PROJ_EUNSUPPORTED;
+    if ((((uintptr_t)spec) & 15) || (((uintptr_t)gz) & 15) || (((uintptr_t)workspace) & 255)) return MONC_PROJ_EINVAL;
+    ProjParams q = make_params(plan, spec, spec, spec, nullptr, nullptr, nullptr, nullptr, workspace);
+    q.ny = j1 - j0;
+    q.ky_base = j0;
+    q.S = spec;
+    q.G = gz;
+    const long long ncol = (long long)q.ny * ((plan->nxh + 31) & ~31);
+    cudaStream_t st = (cudaStream_t)stream;
+    const KernelFn tri = plan->precision == MONC_PROJ_FP64 ? pick_tridiag<double>() : pick_tridiag<float>();
+    tri<<<(unsigned)((ncol + kTriThreads - 1) / kTriThreads), kTriThreads, 0, st>>>(q);
+    return cudaGetLastError() == cudaSuccess ? MONC_PROJ_OK : MONC_PROJ_ECUDA;
+}
+
+int monc_proj_inverse_slab(monc_proj_plan_t plan, int k0, int k1, const void* phat, const void* gz, const void* u,
+                           const void* v, const void* w, void* u_out, void* v_out, void* w_out, void* workspace,
+                           void* stream) {
+    if (!plan || !phat || !gz || !u || !v || !w || !u_out || !v_out || !w_out || !workspace) return MONC_PROJ_EINVAL;
+    if (k0 < 0 || k1 <= k0 || k1 > plan->nz) return MONC_PROJ_EINVAL;
+    if (!slab_plan_ok(plan)) return MONC_PROJ_EUNSUPPORTED;
+    const void* ptrs[] = {phat, gz, u, v, w, u_out, v_out, w_out};
+    for (const void* x : ptrs)
+        if (((uintptr_t)x) & 15) return MONC_PROJ_EINVAL;
+    if (((uintptr_t)workspace) & 255) return MONC_PROJ_EINVAL;
+    ProjParams q = make_params(plan, u, v, w, u_out, v_out, w_out, nullptr, workspace);
+    q.nz = k1 - k0;
+    q.kbase = k0;
+    q.S = const_cast<void*>(phat);
+    q.G = const_cast<void*>(gz);
+    cudaStream_t st = (cudaStream_t)stream;
+    return plan->precision == MONC_PROJ_FP64 ? launch_inverse_slab<double>(plan, q, st)
+                                             : launch_inverse_slab<float>(plan, q, st);
+}
+
+static int pencil_reorder(monc_proj_plan_t plan, int nzl, int parts, const void* src, void* dst, int dir,
+                          void* stream) {
+    if (!plan || !src || !dst || nzl < 1 || nzl > plan->nz || parts < 1) return MONC_PROJ_EINVAL;
+    if ((((uintptr_t)src) & 15) || (((uintptr_t)dst) & 15)) return MONC_PROJ_EINVAL;
+    if (!slab_plan_ok(plan)) return MONC_PROJ_EUNSUPPORTED;
+    const int units = (int)((size_t)plan->nxp * spec_elem(plan) / 16);
+    k_pencil_pack<<<(unsigned)(nzl * plan->ny), 128, 0, (cudaStream_t)stream>>>((const float4*)src, (float4*)dst,
+                                                                               plan->ny, nzl, parts, units, dir);
+    return cudaGetLastError() == cudaSuccess ? MONC_PROJ_OK : MONC_PROJ_ECUDA;
+}
+
+int monc_proj_pack_pencils(monc_proj_plan_t plan, int nzl, int parts, const void* slab, void* packed, void* stream) {
+    return pencil_reorder(plan, nzl, parts, slab, packed, 0, stream);
+}
+
+int monc_proj_unpack_pencils(monc_proj_plan_t plan, int nzl, int parts, const void* packed, void* slab,
+                             void* stream) {
+    return pencil_reorder(plan, nzl, parts, packed, slab, 1, stream);
 }
 
 int monc_proj_krylov_workspace_size(monc_proj_plan_t plan, size_t* bytes) {

@@ -49,6 +49,8 @@ EXPORTS = [
     "monc_proj_profile", "monc_proj_profile_read", "monc_proj_phase_name",
     "monc_proj_solve_noalloc", "monc_proj_autotune", "monc_proj_host_staging_size", "monc_proj_solve_host",
     "monc_proj_krylov_workspace_size", "monc_proj_solve_krylov", "monc_proj_set_allocator",
+    "monc_proj_spectral_pitch", "monc_proj_forward_slab", "monc_proj_vertical_pencil", "monc_proj_inverse_slab",
+    "monc_proj_pack_pencils", "monc_proj_unpack_pencils",
 ]
 
 # Allocator hooks of plan tables (monc_proj_set_allocator)
@@ -105,6 +107,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.monc_proj_krylov_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
     L.monc_proj_solve_krylov.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, d, i, i, ip, dp, vp]
     L.monc_proj_set_allocator.argtypes = [ALLOC_FN, FREE_FN, vp]
+    L.monc_proj_spectral_pitch.argtypes = [vp, ip]
+    L.monc_proj_forward_slab.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp]
+    L.monc_proj_vertical_pencil.argtypes = [vp, i, i, vp, vp, vp, vp]
+    L.monc_proj_inverse_slab.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.monc_proj_pack_pencils.argtypes = [vp, i, i, vp, vp, vp]
+    L.monc_proj_unpack_pencils.argtypes = [vp, i, i, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("monc_proj_status_string", "monc_proj_phase_name"):
             getattr(L, name).restype = ctypes.c_int
@@ -294,6 +302,55 @@ def monc_proj_solve_noalloc(nx, ny, nz, dx, dy, dz, rho_c, rho_f, precision, u, 
 
 
 _allocator_refs = None
+
+
+def monc_proj_spectral_pitch(plan: int) -> int:
+    """Row pitch (complex values) of the plan's spectral arrays."""
+    n = ctypes.c_int()
+    _check(load_library().monc_proj_spectral_pitch(ctypes.c_void_p(plan), ctypes.byref(n)),
+           "monc_proj_spectral_pitch")
+    return n.value
+
+
+def _ptr(t):
+    return ctypes.c_void_p(None if t is None else t.data_ptr())
+
+
+def monc_proj_forward_slab(plan: int, k0, k1, u, v, w, dhat, workspace, stream=None):
+    """Enqueue a1-a2 on levels [k0, k1): dhat receives the slab's spectrum."""
+    rc = load_library().monc_proj_forward_slab(ctypes.c_void_p(plan), int(k0), int(k1), _ptr(u), _ptr(v),
+                                               _ptr(w), _ptr(dhat), _ptr(workspace),
+                                               ctypes.c_void_p(_stream_handle(stream)))
+    _check(rc, "monc_proj_forward_slab")
+
+
+def monc_proj_vertical_pencil(plan: int, j0, j1, spec, gz, workspace, stream=None):
+    """Enqueue a3 on spectral rows [j0, j1): spec D^ -> p^ in place, gz^ out."""
+    rc = load_library().monc_proj_vertical_pencil(ctypes.c_void_p(plan), int(j0), int(j1), _ptr(spec), _ptr(gz),
+                                                  _ptr(workspace), ctypes.c_void_p(_stream_handle(stream)))
+    _check(rc, "monc_proj_vertical_pencil")
+
+
+def monc_proj_inverse_slab(plan: int, k0, k1, phat, gz, u, v, w, u_out, v_out, w_out, workspace, stream=None):
+    """Enqueue a4-a5 on levels [k0, k1)."""
+    rc = load_library().monc_proj_inverse_slab(ctypes.c_void_p(plan), int(k0), int(k1), _ptr(phat), _ptr(gz),
+                                               _ptr(u), _ptr(v), _ptr(w), _ptr(u_out), _ptr(v_out), _ptr(w_out),
+                                               _ptr(workspace), ctypes.c_void_p(_stream_handle(stream)))
+    _check(rc, "monc_proj_inverse_slab")
+
+
+def monc_proj_pack_pencils(plan: int, nzl, parts, slab, packed, stream=None):
+    """Enqueue slab [nzl][ny][nxp] -> per-part row blocks (all-to-all send buffer)."""
+    rc = load_library().monc_proj_pack_pencils(ctypes.c_void_p(plan), int(nzl), int(parts), _ptr(slab),
+                                               _ptr(packed), ctypes.c_void_p(_stream_handle(stream)))
+    _check(rc, "monc_proj_pack_pencils")
+
+
+def monc_proj_unpack_pencils(plan: int, nzl, parts, packed, slab, stream=None):
+    """Enqueue per-part row blocks (all-to-all receive buffer) -> slab [nzl][ny][nxp]."""
+    rc = load_library().monc_proj_unpack_pencils(ctypes.c_void_p(plan), int(nzl), int(parts), _ptr(packed),
+                                                 _ptr(slab), ctypes.c_void_p(_stream_handle(stream)))
+    _check(rc, "monc_proj_unpack_pencils")
 
 
 def monc_proj_set_allocator(alloc=None, release=None):
