@@ -634,7 +634,8 @@ def main():
 def measure_batch(dev, stream, count=64, reps=5, check=True):
     """64 uneven projections (n from {64,96,128,192,256}, nz from
     {64,96,128,160}, mixed precision, seed 3): time of one batched call and of
-    a CUDA-graph replay of it."""
+    a CUDA-graph replay of it, with per-instance launches on the stream pool
+    and with grouped launches (one launch per phase and size group)."""
     import torch
     from paper_2009_12849_gb300 import monc_proj as MP
     from paper_2009_12849_gb300 import workloads as W
@@ -648,13 +649,13 @@ def measure_batch(dev, stream, count=64, reps=5, check=True):
     pts = sum(g.npoints for g in grids)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def timed():
+    def timed(grouped=False):
         for _ in range(2):
-            B.solve(args, stream=stream)
+            B.solve(args, stream=stream, grouped=grouped)
         torch.cuda.synchronize(dev)
         e0.record(stream)
         for _ in range(reps):
-            B.solve(args, stream=stream)
+            B.solve(args, stream=stream, grouped=grouped)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1) / reps
@@ -662,7 +663,7 @@ def measure_batch(dev, stream, count=64, reps=5, check=True):
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.stream(side):
             with torch.cuda.graph(graph, stream=side):
-                B.solve(args, stream=side)
+                B.solve(args, stream=side, grouped=grouped)
         graph.replay()
         torch.cuda.synchronize(dev)
         e0.record(stream)
@@ -673,6 +674,11 @@ def measure_batch(dev, stream, count=64, reps=5, check=True):
         return ms, e0.elapsed_time(e1) / reps
 
     ms0, ms_graph0 = timed()
+    gms0, gms_graph0 = timed(grouped=True)
+    grouped_out = [tuple(t.clone() for t in a[3:6]) for a in args]
+    B.solve(args, stream=stream)
+    torch.cuda.synchronize(dev)
+    grouped_same = all(torch.equal(x, y) for a, o in zip(args, grouped_out) for x, y in zip(a[3:6], o))
     # task shapes picked per instance by the library's autotuner, then timed again
     shapes = B.autotune(args, stream=stream)
     torch.cuda.synchronize(dev)
@@ -682,7 +688,11 @@ def measure_batch(dev, stream, count=64, reps=5, check=True):
     res = {"instances": count, "points": pts, "ms_per_batch": ms, "mpts_per_s": pts / (ms * 1e-3) / 1e6,
            "graph_ms_per_batch": ms_graph, "graph_mpts_per_s": pts / (ms_graph * 1e-3) / 1e6,
            "autotuned": True, "shapes_kept": [list(x) for x in tuned],
-           "default_shapes": {"ms_per_batch": ms0, "graph_ms_per_batch": ms_graph0}}
+           "default_shapes": {"ms_per_batch": ms0, "graph_ms_per_batch": ms_graph0},
+           "grouped": {"api": "monc_proj_solve_batch_grouped (one launch per phase and size group)",
+                       "ms_per_batch": gms0, "graph_ms_per_batch": gms_graph0,
+                       "graph_mpts_per_s": pts / (gms_graph0 * 1e-3) / 1e6,
+                       "bitwise_equal_to_per_instance": grouped_same}}
     if check:
         # every instance against its own FP64 GPU solve (the path the parity
         # tests pin to the FP64 oracle) and its divergence residual

@@ -221,6 +221,23 @@ int monc_proj_solve_batch(const monc_proj_plan_t* plans, const monc_proj_fields*
                           int count, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * The same batch in grouped launches: the instances that share the
+ * horizontal size, the task shapes and whether phi is requested form a
+ * group, and each phase of the projection runs as one launch per group
+ * (chunks of up to 20 instances) whose blocks cover every instance's tasks,
+ * instance after instance; the groups run concurrently on the internal
+ * stream pool.  Instances of FP32 mixed plans with compile-time transform
+ * lengths (64, 96, 128, 192, 256, 512, 1024) and the default kernels are
+ * grouped; any other instance runs as in monc_proj_solve_batch.  Each
+ * instance's parameters travel in the launches' parameters (nothing is
+ * uploaded), so the call may be captured into a CUDA graph on `stream`.
+ * Results equal monc_proj_solve's bit for bit.  Arguments, workspace layout
+ * and errors as monc_proj_solve_batch; the workspace must be 256-byte aligned.
+ */
+int monc_proj_solve_batch_grouped(const monc_proj_plan_t* plans, const monc_proj_fields* fields,
+                                  int count, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * Synchronise `stream` and report (then clear) the plan's latched device
  * error: MONC_PROJ_OK, MONC_PROJ_ETIMEOUT or MONC_PROJ_EDEVICE.
  */

@@ -13,7 +13,7 @@ LIB = os.path.join(HERE, "libmonc_proj.so")
 # group of extended FP32 lengths and part (rows / columns)
 SOURCES = [(f, [], os.path.splitext(f)[0]) for f in
            ("monc_proj.cu", "kern_f32_rows.cu", "kern_f32_cols.cu", "kern_f32_fused.cu", "kern_f64.cu",
-            "kern_f32_refined.cu", "kern_krylov.cu", "kern_f32_pipe.cu", "kern_f32_tc.cu")]
+            "kern_f32_refined.cu", "kern_krylov.cu", "kern_f32_pipe.cu", "kern_f32_tc.cu", "kern_f32_group.cu")]
 SOURCES += [("kern_f32_ext.cu", [f"-DMP_EXT_GROUP={g}", f"-DMP_EXT_PART={part}"], f"kern_f32_ext{g}_{part}")
             for g in (1, 2, 3, 4) for part in (0, 1)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -40,6 +40,46 @@ template <typename C> MP_HD C cmul_si(C a, int s) {
     C c; if (s > 0) { c.x = -a.y; c.y = a.x; } else { c.x = a.y; c.y = -a.x; } return c;
 }
 
+// FP32 complex values on sm_100 and later: the two parts of an add, subtract
+// or real scale go through one paired-FP32 instruction (add/sub/mul .f32x2 on
+// the register pair holding the value), halving the instructions of the
+// butterflies' additions.  Each lane rounds as the scalar operation would.
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000) && !defined(MP_SCALAR_F32)
+#define MP_PAIRED_F32 1
+__device__ __forceinline__ unsigned long long f2bits(float2 a) {
+    return ((unsigned long long)__float_as_uint(a.y) << 32) | __float_as_uint(a.x);
+}
+__device__ __forceinline__ float2 bits2f(unsigned long long b) {
+    return make_float2(__uint_as_float((unsigned)b), __uint_as_float((unsigned)(b >> 32)));
+}
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2bits(a)), "l"(f2bits(b)));
+    return bits2f(d);
+}
+#endif
+MP_HD float2 cadd(float2 a, float2 b) {
+#ifdef MP_PAIRED_F32
+    return __fadd2_rn(a, b);
+#else
+    a.x += b.x; a.y += b.y; return a;
+#endif
+}
+MP_HD float2 csub(float2 a, float2 b) {
+#ifdef MP_PAIRED_F32
+    return f2sub(a, b);
+#else
+    a.x -= b.x; a.y -= b.y; return a;
+#endif
+}
+MP_HD float2 cscale(float2 a, float s) {
+#ifdef MP_PAIRED_F32
+    return __fmul2_rn(a, make_float2(s, s));
+#else
+    a.x *= s; a.y *= s; return a;
+#endif
+}
+
 // Length-R DFTs on registers, exponent sign S (-1 forward, +1 inverse).
 template <typename R, int S> struct Dft2 {
     static MP_HD void run(cplx<R>* x) {
@@ -134,6 +174,14 @@ struct FftFactors {
 // keeps the stride-R accesses of the first stages free of bank conflicts.
 __device__ __forceinline__ int spad(int i) { return i + (i >> 5); }
 __host__ __device__ inline int spad_len(int n) { return n + (n >> 5) + 1; }
+// spad(i0 + r * STRIDE) for i0 >= 0: with STRIDE a multiple of 32 it is
+// spad(i0) + r * (STRIDE + STRIDE / 32), so a butterfly's RAD accesses are one
+// index computation plus compile-time offsets.
+template <int STRIDE>
+__device__ __forceinline__ int spad_at(int sp0, int i0, int r) {
+    if constexpr (STRIDE % 32 == 0) return sp0 + r * (STRIDE + STRIDE / 32);
+    else return spad(i0 + r * STRIDE);
+}
 
 // Twiddle tables: stage s of a length-n plan owns entries [s*n, s*n + R*Ns)
 // of the plan's table, laid out [r][k]: entry r*Ns + k = W_{Ns R}^{r k}, so
@@ -309,8 +357,9 @@ __device__ __forceinline__ void ct_stage(cplx<R>* buf, int nb, int bstride, cons
             const int b = t / NQ;
             const int q = t - b * NQ;
             const cplx<R>* src = buf + b * bstride;
+            const int sq = spad(q);
 #pragma unroll
-            for (int r = 0; r < RAD; ++r) x[i][r] = src[spad(q + r * NQ)];
+            for (int r = 0; r < RAD; ++r) x[i][r] = src[spad_at<NQ>(sq, q, r)];
         }
     }
     Sc::sync();
@@ -332,8 +381,9 @@ __device__ __forceinline__ void ct_stage(cplx<R>* buf, int nb, int bstride, cons
             RegFFT<R, RAD, S>::run(x[i]);
             cplx<R>* dst = buf + b * bstride;
             const int base = qd * NS * RAD + k;
+            const int sb = spad(base);
 #pragma unroll
-            for (int r = 0; r < RAD; ++r) dst[spad(base + r * NS)] = x[i][r];
+            for (int r = 0; r < RAD; ++r) dst[spad_at<NS>(sb, base, r)] = x[i][r];
         }
     }
     Sc::sync();
@@ -417,8 +467,15 @@ __device__ __forceinline__ void ct_first(cplx<R>* buf, int nb, int bstride, Load
             bfly_map<BFAST, NQ>(t, nb, b, q);
             RegFFT<R, RAD, S>::run(x[i]);
             cplx<R>* dst = buf + b * bstride;
+            if constexpr (RAD % 32 == 0) {
+                // spad(q RAD + r) = q (RAD + RAD/32) + r + r/32
+                cplx<R>* d0 = dst + q * (RAD + RAD / 32);
 #pragma unroll
-            for (int r = 0; r < RAD; ++r) dst[spad(q * RAD + r)] = x[i][r];
+                for (int r = 0; r < RAD; ++r) d0[r + (r >> 5)] = x[i][r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < RAD; ++r) dst[spad(q * RAD + r)] = x[i][r];
+            }
         }
     }
     Sc::sync();
@@ -454,8 +511,9 @@ __device__ __forceinline__ void ct_last(const cplx<R>* buf, int nb, int bstride,
             bfly_map<BFAST, NQ>(t, nb, b, q);
             const cplx<R>* src = buf + b * bstride;
             cplx<R> x[RAD];
+            const int sq = spad(q);
 #pragma unroll
-            for (int r = 0; r < RAD; ++r) x[r] = src[spad(q + r * NQ)];
+            for (int r = 0; r < RAD; ++r) x[r] = src[spad_at<NQ>(sq, q, r)];
             // last stage: Ns * RAD = N, so q < Ns and q is the twiddle index k
             if (NS > 1) {
 #pragma unroll
@@ -502,8 +560,9 @@ __device__ __forceinline__ void ct_last_pre(const cplx<R>* buf, int nb, int bstr
             bfly_map<BFAST, NQ>(t, nb, b, q);
             const cplx<R>* src = buf + b * bstride;
             cplx<R> x[RAD];
+            const int sq = spad(q);
 #pragma unroll
-            for (int r = 0; r < RAD; ++r) x[r] = src[spad(q + r * NQ)];
+            for (int r = 0; r < RAD; ++r) x[r] = src[spad_at<NQ>(sq, q, r)];
             if (NS > 1) {
 #pragma unroll
                 for (int r = 1; r < RAD; ++r) {
@@ -539,8 +598,9 @@ __device__ __forceinline__ void ct_last_sync(const cplx<R>* buf, int nb, int bst
             int b, q;
             bfly_map<BFAST, NQ>(t, nb, b, q);
             const cplx<R>* src = buf + b * bstride;
+            const int sq = spad(q);
 #pragma unroll
-            for (int r = 0; r < RAD; ++r) x[i][r] = src[spad(q + r * NQ)];
+            for (int r = 0; r < RAD; ++r) x[i][r] = src[spad_at<NQ>(sq, q, r)];
             if (NS > 1) {
 #pragma unroll
                 for (int r = 1; r < RAD; ++r) {

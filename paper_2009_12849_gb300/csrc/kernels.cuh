@@ -115,7 +115,7 @@ template <typename R, int NX, typename F, bool EF, class Sc>
 __device__ __forceinline__ void fwd_rows_task(const ProjParams& p, unsigned char* smem_raw, int k, int j0,
                                               int rows) {
     using C = cplx<R>;
-    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int nx = p.nx, ny = p.ny;
     const int npair = rows / 2;
     const int bs = p.bs_row;
     C* bufA = (C*)smem_raw;
@@ -282,6 +282,17 @@ __global__ void __launch_bounds__(512) k_fwd_rows(ProjParams p) {
                                             p.rows_fwd);
 }
 
+// Shared-memory pitch of a column tile's transforms (the plan's bs_col): the
+// padded length rounded to 4 (mod 16) complex values, which spreads the
+// columns of a tile over distinct banks.
+template <int NY> struct ColPitch {
+    static constexpr int value = [] {
+        int b = NY + (NY >> 5) + 1;
+        while (b % 16 != 4) ++b;
+        return b;
+    }();
+};
+
 // ---------------------------------------------------------------------------
 // Column transforms along y for a tile of kx columns of one level.
 // DIR = -1: forward (T -> S).  The inverse uses k_inv_cols.
@@ -372,32 +383,35 @@ __device__ __forceinline__ void discard_fwd_tile(const ProjParams& p, int k, int
 }
 
 // One column task of a compile-time length: tile `tile` of level k, T -> S.
-template <typename R, int NY>
+// NXP and TW as in inv_cols_ct_task.
+template <typename R, int NY, int NXP = 0, int TW = 0>
 __device__ __forceinline__ void fwd_cols_task(const ProjParams& p, unsigned char* smem_raw, int k, int tile) {
     using C = cplx<R>;
-    const int kx0 = tile * p.tw_cols;
+    const int nxh = p.nxh;
+    const int nxp = NXP ? NXP : p.nxp;
+    const int tw = TW ? TW : p.tw_cols;
+    const int bs = TW ? ColPitch<NY>::value : p.bs_col;
+    const int kx0 = tile * tw;
     C* buf = (C*)smem_raw;
-    const C* T = (const C*)p.T;
-    C* S = (C*)p.S;
-    const int nxh = p.nxh, nxp = p.nxp, ny = p.ny;
+    const C* T = (const C*)p.T + (size_t)k * NY * nxp + kx0;
+    C* S = (C*)p.S + (size_t)k * NY * nxp + kx0;
     auto load = [&](int c, int j) -> C {
-        const int kx = kx0 + c;
-        return (kx < nxh) ? T[((size_t)k * ny + j) * nxp + kx] : cmk<R>((R)0, (R)0);
+        return (kx0 + c < nxh) ? T[j * nxp + c] : cmk<R>((R)0, (R)0);
     };
-    ct_first<R, NY, -1, true>(buf, p.tw_cols, p.bs_col, load);
+    ct_first<R, NY, -1, true>(buf, tw, bs, load);
     if (p.ho.discard) discard_fwd_tile<R>(p, k, tile);
-    CtMid<R, NY, StageInfo<R, NY, 1>::NEXT, -1>::run(buf, p.tw_cols, p.bs_col, ctab<R>(p.twy));
+    CtMid<R, NY, StageInfo<R, NY, 1>::NEXT, -1>::run(buf, tw, bs, ctab<R>(p.twy));
     auto store = [&](int c, int q, const C* x, int ns) {
-        const int kx = kx0 + c;
-        if (kx >= nxh) return;
+        if (kx0 + c >= nxh) return;
         constexpr int RAD = StageInfo<R, NY, LastNs<R, NY>::value>::RAD;
+        C* d = S + q * nxp + c;
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) S[((size_t)k * ny + q + r * ns) * nxp + kx] = x[r];
+        for (int r = 0; r < RAD; ++r) d[r * ns * nxp] = x[r];
     };
-    ct_last<R, NY, -1, true>(buf, p.tw_cols, p.bs_col, ctab<R>(p.twy), store);
+    ct_last<R, NY, -1, true>(buf, tw, bs, ctab<R>(p.twy), store);
 }
 
-template <typename R, int NY>
+template <typename R, int NY, int NXP = 0, int TW = 0>
 __global__ void __launch_bounds__(512) k_fwd_cols(ProjParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using C = cplx<R>;
@@ -405,7 +419,7 @@ __global__ void __launch_bounds__(512) k_fwd_cols(ProjParams p) {
     const int k = kl;
     const int tile = blockIdx.x - kl * p.ntiles;
     if constexpr (NY > 0) {
-        fwd_cols_task<R, NY>(p, smem_raw, k, tile);
+        fwd_cols_task<R, NY, NXP, TW>(p, smem_raw, k, tile);
     } else {
         C* buf = (C*)smem_raw;
         load_cols<R>(buf, (const C*)p.T, k, tile * p.tw_cols, p, nullptr);
@@ -679,10 +693,10 @@ __device__ __forceinline__ void tridiag_column_ckpt32(const ProjParams& p, size_
 // spill more registers.
 constexpr int kTriThreads = 128;
 
+// Column `col` of the launch (rows of nxw = nxh rounded up to 32 columns).
 template <typename R>
-__global__ void __launch_bounds__(kTriThreads, 1024 / kTriThreads) k_tridiag(ProjParams p) {
+__device__ __forceinline__ void tridiag_task(const ProjParams& p, long long col) {
     const int nxw = (p.nxh + 31) & ~31;
-    const long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int r = (int)(col / nxw);
     const int kx = (int)(col - (long long)r * nxw);
     if (r >= p.ny || kx >= p.nxh) return;
@@ -700,6 +714,11 @@ __global__ void __launch_bounds__(kTriThreads, 1024 / kTriThreads) k_tridiag(Pro
         else if (p.nz <= kTriSeg * kTriMaxSeg) tridiag_column_ckpt32(p, base, (float)lam);
         else tridiag_column_inplace<float>(p, base, (float)lam, mean);
     }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kTriThreads, 1024 / kTriThreads) k_tridiag(ProjParams p) {
+    tridiag_task<R>(p, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -732,67 +751,79 @@ __device__ __forceinline__ InvColField<R> inv_col_field(const ProjParams& p, int
 // Compile-time lengths: task = (level, tile, kind); kind 0 reads the p^ tile
 // and writes every field derived from it (x-gradient with ex, y-gradient,
 // phi if requested; the re-reads of the tile hit L2), kind 1 transforms gz^.
-template <typename R, int NY>
-__device__ __forceinline__ void inv_cols_ct_task(const ProjParams& p, int k, int kx0, int f, cplx<R>* buf) {
+// F (the field, as inv_col_field) is a template argument so that the loads
+// and stores carry no run-time branch; NXP and TW, when non-zero, are the
+// spectral row pitch and the tile width known at compile time (square grids
+// with the default tiles), which turns the element addresses into constant
+// offsets from one per-thread pointer.
+template <typename R, int NY, int F, int NXP = 0, int TW = 0>
+__device__ __forceinline__ void inv_cols_ct_task(const ProjParams& p, int k, int kx0, cplx<R>* buf) {
     using C = cplx<R>;
-    const InvColField<R> fd = inv_col_field<R>(p, f, k);
-    const int nxh = p.nxh, nxp = p.nxp, ny = p.ny;
-    const C* src = fd.src + (size_t)k * ny * nxp;
-    const C* ey = fd.ey;
+    const int nxh = p.nxh;
+    const int nxp = NXP ? NXP : p.nxp;
+    const int tw = TW ? TW : p.tw_cols;
+    const int bs = TW ? ColPitch<NY>::value : p.bs_col;
+    const C* src = (F == 2 ? (const C*)p.G : (const C*)p.S) + (size_t)k * NY * nxp + kx0;
+    const C* ey = ctab<R>(p.ey);
     auto load = [&](int c, int j) -> C {
-        const int kx = kx0 + c;
-        if (kx >= nxh) return cmk<R>((R)0, (R)0);
-        const C v = src[(size_t)j * nxp + kx];
-        return ey ? cmul(v, ey[j]) : v;
+        if (kx0 + c >= nxh) return cmk<R>((R)0, (R)0);
+        const C v = src[j * nxp + c];
+        if constexpr (F == 1) return cmul(v, ey[j]);
+        else return v;
     };
-    ct_first<R, NY, 1, true>(buf, p.tw_cols, p.bs_col, load);
-    CtMid<R, NY, StageInfo<R, NY, 1>::NEXT, 1>::run(buf, p.tw_cols, p.bs_col, ctab<R>(p.twy));
+    ct_first<R, NY, 1, true>(buf, tw, bs, load);
+    CtMid<R, NY, StageInfo<R, NY, 1>::NEXT, 1>::run(buf, tw, bs, ctab<R>(p.twy));
     const C* ex = ctab<R>(p.ex);
-    const bool mul_ex = fd.ex;
-    C* dst = fd.dst + (size_t)k * ny * nxp;
+    C* dst = (F == 0 ? (C*)p.Tp : F == 1 ? (C*)p.Tgy : F == 2 ? (C*)p.Tgz : (C*)p.Tphi) + (size_t)k * NY * nxp + kx0;
     auto store = [&](int c, int q, const C* x, int ns) {
-        const int kx = kx0 + c;
-        if (kx >= nxh) return;
+        if (kx0 + c >= nxh) return;
         constexpr int RAD = StageInfo<R, NY, LastNs<R, NY>::value>::RAD;
-        const C e = mul_ex ? ex[kx] : cmk<R>((R)1, (R)0);
+        C* d = dst + q * nxp + c;
+        if constexpr (F == 0) {
+            const C e = ex[kx0 + c];
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) dst[(size_t)(q + r * ns) * nxp + kx] = mul_ex ? cmul(x[r], e) : x[r];
+            for (int r = 0; r < RAD; ++r) d[r * ns * nxp] = cmul(x[r], e);
+        } else {
+#pragma unroll
+            for (int r = 0; r < RAD; ++r) d[r * ns * nxp] = x[r];
+        }
     };
-    ct_last<R, NY, 1, true>(buf, p.tw_cols, p.bs_col, ctab<R>(p.twy), store);
+    ct_last<R, NY, 1, true>(buf, tw, bs, ctab<R>(p.twy), store);
 }
 
 // One column task of a compile-time length: tile from kx0 of level k; kind
 // 0 transforms the p^ tile (x- and y-gradient, and phi if requested; with
 // PHI the potential alone), kind 1 the gz^ tile.
-template <typename R, int NY, bool PHI>
+template <typename R, int NY, bool PHI, int NXP = 0, int TW = 0>
 __device__ __forceinline__ void inv_cols_tile(const ProjParams& p, unsigned char* smem_raw, int k, int kx0,
                                               int kind) {
     cplx<R>* buf = (cplx<R>*)smem_raw;
     if constexpr (PHI) {
-        if (kind == 0) inv_cols_ct_task<R, NY>(p, k, kx0, 3, buf);
+        if (kind == 0) inv_cols_ct_task<R, NY, 3, NXP, TW>(p, k, kx0, buf);
     } else if (kind == 0) {
-        inv_cols_ct_task<R, NY>(p, k, kx0, 0, buf);
+        inv_cols_ct_task<R, NY, 0, NXP, TW>(p, k, kx0, buf);
         __syncthreads();
-        inv_cols_ct_task<R, NY>(p, k, kx0, 1, buf);
+        inv_cols_ct_task<R, NY, 1, NXP, TW>(p, k, kx0, buf);
         if (p.nch == 4) {
             __syncthreads();
-            inv_cols_ct_task<R, NY>(p, k, kx0, 3, buf);
+            inv_cols_ct_task<R, NY, 3, NXP, TW>(p, k, kx0, buf);
         }
     } else if (p.kbase + k > 0) {
-        inv_cols_ct_task<R, NY>(p, k, kx0, 2, buf);
+        inv_cols_ct_task<R, NY, 2, NXP, TW>(p, k, kx0, buf);
     }
 }
 
 // PHI: the potential alone (refinement passes): kind 0 transforms the p^ tile
 // into Tphi, kind 1 does nothing.
-template <typename R, int NY, bool PHI = false>
+template <typename R, int NY, bool PHI = false, int NXP = 0, int TW = 0>
 __global__ void __launch_bounds__(512) k_inv_cols(ProjParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using C = cplx<R>;
     if constexpr (NY > 0) {
         const int task = blockIdx.x >> 1;
         const int kl = task / p.ntiles;
-        inv_cols_tile<R, NY, PHI>(p, smem_raw, kl, (task - kl * p.ntiles) * p.tw_cols, blockIdx.x & 1);
+        const int tw = TW ? TW : p.tw_cols;
+        inv_cols_tile<R, NY, PHI, NXP, TW>(p, smem_raw, kl, (task - kl * p.ntiles) * tw, blockIdx.x & 1);
         return;
     }
     const int nf = p.nch;
@@ -865,7 +896,7 @@ template <typename R, int NX, typename F, bool EF, class Sc>
 __device__ __forceinline__ void inv_rows_ct(const ProjParams& p, unsigned char* smem_raw, int k, int j0, int ch,
                                             int rows) {
     using C = cplx<R>;
-    const int ny = p.ny, nz = p.nz;
+    const int ny = p.ny;
     const int bs = p.bs_row;
     C* bufA = (C*)smem_raw;
     const size_t plane = (size_t)ny * NX;

@@ -9,6 +9,8 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -17,6 +19,7 @@
 
 #include "krylov.h"
 #include "pickers.h"
+#include "group.cuh"
 #include "pipe.cuh"
 
 using namespace mp;
@@ -351,11 +354,17 @@ struct SolveKernels {
 template <typename R> SolveKernels pick_kernels(const monc_proj_plan_s* p) {
     const int nx = p->nx, ny = p->ny;
     const bool ref = p->precision == MONC_PROJ_REFINED;
-    return SolveKernels{ref ? pick_refined_fwd_rows(nx) : pick_k_fwd_rows<R>(nx),
-                        pick_k_fwd_cols<R>(ny),
-                        ref ? pick_refined_inv_cols(ny)
-                            : p->persist_cols ? pick_inv_cols_persist<R>(ny) : pick_k_inv_cols<R>(ny),
-                        ref ? pick_refined_inv_rows(nx) : pick_k_inv_rows<R>(nx)};
+    SolveKernels ks{ref ? pick_refined_fwd_rows(nx) : pick_k_fwd_rows<R>(nx),
+                    pick_k_fwd_cols<R>(ny),
+                    ref ? pick_refined_inv_cols(ny)
+                        : p->persist_cols ? pick_inv_cols_persist<R>(ny) : pick_k_inv_cols<R>(ny),
+                    ref ? pick_refined_inv_rows(nx) : pick_k_inv_rows<R>(nx)};
+    if (sizeof(R) == 4) {
+        if (KernelFn f = pick_cols_square_f32(ny, p->nxp, p->tw_cols, p->bs_col, false)) ks.fwd_cols = f;
+        if (!ref && !p->persist_cols)
+            if (KernelFn f = pick_cols_square_f32(ny, p->nxp, p->tw_cols, p->bs_col, true)) ks.inv_cols = f;
+    }
+    return ks;
 }
 
 // ---------------------------------------------------------------------------
@@ -1370,6 +1379,147 @@ int monc_proj_solve_batch(const monc_proj_plan_t* plans, const monc_proj_fields*
         if (r && !first_error) first_error = r;
     }
     // join: the caller's stream waits for every pool stream used
+    for (int j = 0; j < nstreams; ++j) {
+        if (cudaEventRecord(pool->join[j], pool->s[j]) != cudaSuccess ||
+            cudaStreamWaitEvent(st, pool->join[j], 0) != cudaSuccess) {
+            cudaGetLastError();
+            return MONC_PROJ_ECUDA;
+        }
+    }
+    return first_error;
+}
+
+// ---------------------------------------------------------------------------
+// Grouped batch: one launch per phase and group of instances (group.cuh).
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+// Plans whose solve is the default FP32 split kernels of compile-time lengths
+bool group_eligible(const monc_proj_plan_s* p) {
+    return p->precision == MONC_PROJ_MIXED && p->ct_rows && p->ct_cols && !p->fused && !p->pipe &&
+           !p->persist_cols && !p->tma_cols && !p->tc_cols && pick_group_f32(0, p->nx) && pick_group_f32(1, p->ny);
+}
+
+// The five phase launches of one chunk of a group (instances idx, all with
+// the task shapes of plans[idx[0]]) on stream st.
+int launch_group_chunk(const monc_proj_plan_t* plans, const monc_proj_fields* fields, const std::vector<int>& idx,
+                       const std::vector<size_t>& off, unsigned char* ws, cudaStream_t st) {
+    const monc_proj_plan_s* p0 = plans[idx[0]];
+    const int m = (int)idx.size();
+    std::unique_ptr<GroupArgs> a(new (std::nothrow) GroupArgs());
+    if (!a) return MONC_PROJ_ENOMEM;
+    a->n = m;
+    for (int j = 0; j < m; ++j) {
+        const int i = idx[j];
+        const monc_proj_fields& f = fields[i];
+        a->p[j] = make_params(plans[i], f.u, f.v, f.w, f.u_out, f.v_out, f.w_out, f.phi_out, ws + off[i]);
+    }
+    const int inv_idx = a->p[0].nch == 4 ? 1 : 0;
+    const long long ncol = (long long)p0->ny * ((p0->nxh + 31) & ~31);
+    for (int phase = 0; phase < 5; ++phase) {
+        int thr = 0;
+        size_t smem = 0;
+        a->start[0] = 0;
+        for (int j = 0; j < m; ++j) {
+            const ProjParams& q = a->p[j];
+            long long nb = 0;
+            switch (phase) {
+                case 0: nb = (long long)q.nz * p0->nrb_fwd; break;
+                case 1: nb = (long long)q.nz * p0->ntiles; break;
+                case 2: nb = (ncol + kTriThreads - 1) / kTriThreads; break;
+                case 3: nb = (long long)q.nz * p0->ntiles * 2; break;
+                default: nb = (long long)q.nz * q.nrb_inv * q.nch; break;
+            }
+            if (a->start[j] + nb > 0x7fffffffLL) return MONC_PROJ_EUNSUPPORTED;
+            a->start[j + 1] = a->start[j] + (int)nb;
+        }
+        switch (phase) {
+            case 0: thr = p0->thr_fwd_rows; smem = p0->smem_fwd_rows; break;
+            case 1: thr = p0->thr_cols; smem = p0->smem_fcols; break;
+            case 2: thr = kTriThreads; smem = 0; break;
+            case 3: thr = p0->thr_cols; smem = p0->smem_cols; break;
+            default: thr = p0->thr_inv_rows[inv_idx]; smem = p0->smem_inv_rows[inv_idx]; break;
+        }
+        const GroupFn fn = pick_group_f32(phase, (phase == 0 || phase == 4) ? p0->nx : p0->ny);
+        if (!fn) return MONC_PROJ_EUNSUPPORTED;
+        if (smem > 48 * 1024 &&
+            cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            return MONC_PROJ_ECUDA;
+        }
+        if (a->start[m] > 0) fn<<<a->start[m], thr, smem, st>>>(*a);
+        if (cudaGetLastError() != cudaSuccess) return MONC_PROJ_ECUDA;
+    }
+    return MONC_PROJ_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int monc_proj_solve_batch_grouped(const monc_proj_plan_t* plans, const monc_proj_fields* fields, int count,
+                                  void* workspace, size_t workspace_bytes, void* stream) {
+    if (!plans || !fields || count < 0 || (count > 0 && !workspace)) return MONC_PROJ_EINVAL;
+    size_t need = 0;
+    int rc = monc_proj_batch_workspace_size(plans, count, &need);
+    if (rc) return rc;
+    if (workspace_bytes < need || (((uintptr_t)workspace) & 255)) return MONC_PROJ_EINVAL;
+    if (count == 0) return MONC_PROJ_OK;
+    for (int i = 0; i < count; ++i) {
+        const monc_proj_fields& f = fields[i];
+        if (!f.u || !f.v || !f.w || !f.u_out || !f.v_out || !f.w_out) return MONC_PROJ_EINVAL;
+        const void* ptrs[] = {f.u, f.v, f.w, f.u_out, f.v_out, f.w_out, f.phi_out};
+        for (const void* x : ptrs)
+            if (((uintptr_t)x) & 15) return MONC_PROJ_EINVAL;
+    }
+    StreamPool* pool = nullptr;
+    rc = stream_pool(&pool);
+    if (rc) return rc;
+    std::vector<size_t> off(count);
+    size_t o = 0;
+    for (int i = 0; i < count; ++i) {
+        off[i] = o;
+        o += align256(plans[i]->ws_bytes);
+    }
+    // groups: same horizontal size, task shapes and channel count; chunks of
+    // at most kGroupMax instances, largest first within a group
+    std::map<std::vector<int>, std::vector<int>> groups;
+    std::vector<int> singles;
+    for (int i = 0; i < count; ++i) {
+        const monc_proj_plan_s* p = plans[i];
+        if (!group_eligible(p)) {
+            singles.push_back(i);
+            continue;
+        }
+        groups[{p->nx, p->ny, p->row_threads, p->col_threads, fields[i].phi_out ? 4 : 3}].push_back(i);
+    }
+    std::vector<std::vector<int>> chunks;
+    for (auto& g : groups) {
+        std::vector<int>& v = g.second;
+        std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return plans[a]->nz > plans[b]->nz; });
+        for (size_t c = 0; c < v.size(); c += kGroupMax)
+            chunks.emplace_back(v.begin() + c, v.begin() + std::min(v.size(), c + (size_t)kGroupMax));
+    }
+    std::lock_guard<std::mutex> lock(pool->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nstreams = std::min<int>((int)(chunks.size() + singles.size()), kBatchStreams);
+    if (cudaEventRecord(pool->fork, st) != cudaSuccess) { cudaGetLastError(); return MONC_PROJ_ECUDA; }
+    for (int j = 0; j < nstreams; ++j)
+        if (cudaStreamWaitEvent(pool->s[j], pool->fork, 0) != cudaSuccess) { cudaGetLastError(); return MONC_PROJ_ECUDA; }
+    unsigned char* ws = (unsigned char*)workspace;
+    int first_error = MONC_PROJ_OK;
+    int n = 0;
+    for (const auto& c : chunks) {
+        const int r = launch_group_chunk(plans, fields, c, off, ws, pool->s[n++ % nstreams]);
+        if (r && !first_error) first_error = r;
+    }
+    for (int i : singles) {
+        const monc_proj_fields& f = fields[i];
+        const int r = monc_proj_solve(plans[i], f.u, f.v, f.w, f.u_out, f.v_out, f.w_out, f.phi_out, ws + off[i],
+                                      pool->s[n++ % nstreams]);
+        if (r && !first_error) first_error = r;
+    }
     for (int j = 0; j < nstreams; ++j) {
         if (cudaEventRecord(pool->join[j], pool->s[j]) != cudaSuccess ||
             cudaStreamWaitEvent(st, pool->join[j], 0) != cudaSuccess) {

@@ -22,6 +22,16 @@ template <typename R> KernelFn pick_inv_cols_persist(int n);
 template <typename R> KernelFn pick_fwd_fused(int n);
 template <typename R> KernelFn pick_inv_fused(int n);
 template <typename R> KernelFn pick_tridiag();
+// FP32 column kernels with the spectral pitch and tile width fixed at compile
+// time (nx = ny = 256, 512, 1024 with the default tiles); nullptr otherwise
+KernelFn pick_cols_square_f32(int ny, int nxp, int tw, int bs, bool inv);
+// grouped-launch kernels of batched FP32 projections (group.cuh): phase 0..4
+// = forward rows, forward columns, vertical solve, inverse columns, inverse
+// rows, for length n (the rows' nx or the columns' ny; any n for phase 2);
+// nullptr when n has no compile-time plan
+struct GroupArgs;
+using GroupFn = void (*)(const GroupArgs);
+GroupFn pick_group_f32(int phase, int n);
 // FP32 persistent pipelines of the forward and inverse transforms (pipe.cuh);
 // nullptr for grids without them
 // (ef: the variants streaming u, v, w with evict-first L2 priority)

@@ -50,7 +50,7 @@ EXPORTS = [
     "monc_proj_solve_noalloc", "monc_proj_autotune", "monc_proj_host_staging_size", "monc_proj_solve_host",
     "monc_proj_krylov_workspace_size", "monc_proj_solve_krylov", "monc_proj_set_allocator",
     "monc_proj_spectral_pitch", "monc_proj_forward_slab", "monc_proj_vertical_pencil", "monc_proj_inverse_slab",
-    "monc_proj_pack_pencils", "monc_proj_unpack_pencils",
+    "monc_proj_pack_pencils", "monc_proj_unpack_pencils", "monc_proj_solve_batch_grouped",
 ]
 
 # Allocator hooks of plan tables (monc_proj_set_allocator)
@@ -89,6 +89,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.monc_proj_solve.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.monc_proj_batch_workspace_size.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(sz)]
     L.monc_proj_solve_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Fields), i, vp, sz, vp]
+    L.monc_proj_solve_batch_grouped.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Fields), i, vp, sz, vp]
     L.monc_proj_sync_status.argtypes = [vp, vp]
     L.monc_proj_destroy.argtypes = [vp]
     L.monc_proj_status_string.argtypes = [i]
@@ -235,17 +236,26 @@ def monc_proj_batch_workspace_size(plans) -> int:
     return n.value
 
 
-def monc_proj_solve_batch(plans, fields, workspace, stream=None):
-    """fields: list of (u, v, w, u_out, v_out, w_out, phi_out-or-None) tensors."""
+def _batch_call(name, plans, fields, workspace, stream):
     n = len(plans)
     arr = (ctypes.c_void_p * n)(*plans)
     fa = (Fields * n)()
     for i, f in enumerate(fields):
         fa[i] = Fields(*[None if t is None else t.data_ptr() for t in f])
-    rc = load_library().monc_proj_solve_batch(arr, fa, n, ctypes.c_void_p(workspace.data_ptr()),
-                                              workspace.numel() * workspace.element_size(),
-                                              ctypes.c_void_p(_stream_handle(stream)))
-    _check(rc, "monc_proj_solve_batch")
+    rc = getattr(load_library(), name)(arr, fa, n, ctypes.c_void_p(workspace.data_ptr()),
+                                       workspace.numel() * workspace.element_size(),
+                                       ctypes.c_void_p(_stream_handle(stream)))
+    _check(rc, name)
+
+
+def monc_proj_solve_batch(plans, fields, workspace, stream=None):
+    """fields: list of (u, v, w, u_out, v_out, w_out, phi_out-or-None) tensors."""
+    _batch_call("monc_proj_solve_batch", plans, fields, workspace, stream)
+
+
+def monc_proj_solve_batch_grouped(plans, fields, workspace, stream=None):
+    """As monc_proj_solve_batch, one launch per phase and group of instances."""
+    _batch_call("monc_proj_solve_batch_grouped", plans, fields, workspace, stream)
 
 
 def monc_proj_sync_status(plan: int, stream=None) -> int:
@@ -509,12 +519,15 @@ class BatchProjector:
             self.workspace_bytes = monc_proj_batch_workspace_size([p.handle for p in self.plans])
             self.workspace = torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8, device=self.device)
 
-    def solve(self, fields, stream=None):
-        """fields: list of (u, v, w, u_out, v_out, w_out) or (..., phi_out) tensors."""
+    def solve(self, fields, stream=None, grouped=False):
+        """fields: list of (u, v, w, u_out, v_out, w_out) or (..., phi_out)
+        tensors.  grouped: one launch per phase and group of instances
+        (monc_proj_solve_batch_grouped) instead of per-instance launches."""
         if len(fields) != len(self.plans):
             raise ProjError(MONC_PROJ_EINVAL, "BatchProjector.solve")
         full = [tuple(f) + (None,) * (7 - len(f)) for f in fields]
-        monc_proj_solve_batch([p.handle for p in self.plans], full, self.workspace, stream)
+        fn = monc_proj_solve_batch_grouped if grouped else monc_proj_solve_batch
+        fn([p.handle for p in self.plans], full, self.workspace, stream)
 
     def autotune(self, fields, reps=3, stream=None):
         """Tune each instance's plan alone on its fields (inputs left

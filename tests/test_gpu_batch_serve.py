@@ -40,6 +40,62 @@ def test_batch_equals_individual_solves(prec):
     B.close()
 
 
+def test_grouped_batch_equals_individual_solves():
+    """Grouped launches: instances of one size share each phase's launch
+    (a group of 25 spans two chunks); sizes without a compile-time plan and
+    FP64 plans run alone; with and without phi.  Bit for bit against
+    standalone solves, also when the call is captured into a CUDA graph."""
+    mp = _mp()
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(21)
+    spec = [(64, int(rng.integers(3, 12)), "mixed") for _ in range(25)]
+    spec += [(96, 20, "mixed"), (96, 7, "mixed"), (128, 12, "mixed"), (256, 5, "mixed"), (48, 9, "mixed"),
+             (30, 7, "mixed"), (64, 6, "fp64")]
+    plans, fields, refs, ins = [], [], [], []
+    for i, (n, nz, prec) in enumerate(spec):
+        g = W.make_grid(n, n, nz, 25.0, 25.0, W.geometric_dz(nz, 10.0, 100.0))
+        dt = torch.float32 if prec == "mixed" else torch.float64
+        u, v, w = (torch.tensor(a, dtype=dt, device=dev) for a in W.random_fields(g, 70 + i, True))
+        phi = i % 3 == 0
+        P = mp.Projector.from_grid(g, prec, dev)
+        refs.append([t.clone() for t in P.solve(u, v, w, phi=phi)])
+        torch.cuda.synchronize()
+        P.close()
+        pl = mp.Plan(g, prec, dev)
+        plans.append(pl)
+        out = [torch.empty_like(u), torch.empty_like(v), torch.empty_like(w)]
+        if phi:
+            out.append(torch.empty_like(u))
+        fields.append((u, v, w, *out) + (None,) * (4 - len(out)))
+    handles = [p.handle for p in plans]
+    ws = torch.empty(max(mp.monc_proj_batch_workspace_size(handles), 256), dtype=torch.uint8, device=dev)
+    mp.monc_proj_solve_batch_grouped(handles, fields, ws)
+    torch.cuda.synchronize()
+
+    def check():
+        for f, r in zip(fields, refs):
+            got = [t for t in f[3:] if t is not None]
+            assert len(got) == len(r)
+            for x, y in zip(got, r):
+                assert torch.equal(x, y)
+
+    check()
+    for f in fields:
+        for t in f[3:]:
+            if t is not None:
+                t.zero_()
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream(dev)
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            mp.monc_proj_solve_batch_grouped(handles, fields, ws, stream=s)
+    graph.replay()
+    torch.cuda.synchronize()
+    check()
+    for p in plans:
+        p.close()
+
+
 def test_batch_capturable_in_cuda_graph():
     mp = _mp()
     dev = torch.device("cuda", 0)
