@@ -682,12 +682,18 @@ def measure_batch(dev, stream, count=64, reps=5, check=True):
     # task shapes picked per instance by the library's autotuner, then timed again
     shapes = B.autotune(args, stream=stream)
     torch.cuda.synchronize(dev)
+    scheds = {}
+    for pl in B.plans:
+        sc = MP.monc_proj_plan_schedule(pl.handle)
+        key = f"n={pl.grid.nx} rows {sc['row_threads']}thr cols {sc['col_threads']}thr E={sc['col_elems']}"
+        scheds[key] = scheds.get(key, 0) + 1
     ms, ms_graph = timed()
     B.close()
     tuned = sorted({tuple(x) for x in shapes})
     res = {"instances": count, "points": pts, "ms_per_batch": ms, "mpts_per_s": pts / (ms * 1e-3) / 1e6,
            "graph_ms_per_batch": ms_graph, "graph_mpts_per_s": pts / (ms_graph * 1e-3) / 1e6,
            "autotuned": True, "shapes_kept": [list(x) for x in tuned],
+           "schedules_kept": dict(sorted(scheds.items())),
            "default_shapes": {"ms_per_batch": ms0, "graph_ms_per_batch": ms_graph0},
            "grouped": {"api": "monc_proj_solve_batch_grouped (one launch per phase and size group)",
                        "ms_per_batch": gms0, "graph_ms_per_batch": gms_graph0,

@@ -402,22 +402,29 @@ int monc_proj_solve_noalloc(int nx, int ny, int nz, double dx, double dy,
                             void* u_out, void* v_out, void* w_out, void* phi_out, void* stream);
 
 /*
- * monc_proj_autotune -- pick the plan's task shapes by timing them (a tuning
- * step with no counterpart in the paper).
+ * monc_proj_autotune -- pick the plan's task shapes and column radix schedule
+ * by timing them (a tuning step with no counterpart in the paper).
  *
  * For compile-time transform lengths the row kernels take tasks of 32, 64 or
  * 128 threads and the column kernels tiles of 128, 256 or 512 threads (the
- * candidates whose shared memory fits).  Each distinct candidate runs one
+ * candidates whose shared memory fits).  FP32 plans of square 256, 512 and
+ * 1024 grids also try a second radix schedule for the column transforms:
+ * 16 elements per thread (1024 = 16*16*4, three shared-memory passes, fewer
+ * registers and more resident warps) against the default 32 (1024 = 32*32,
+ * two passes), with 256-thread tiles.  Each distinct candidate runs one
  * warm-up solve and `reps` timed solves (3 if reps <= 0) of the caller's
  * fields on `stream`, timed with CUDA events; the fastest is kept in the plan.
  * The call waits for the stream.  The solves write u_out, v_out, w_out (they
- * may alias the inputs only if the inputs may be overwritten).  The shapes
- * decide how the work is split into blocks, never the arithmetic, so the
- * results are bitwise the same with every choice.  The call changes the plan:
- * make it before the plan is shared between threads or solves are captured
- * into a graph.  Plans running an opt-in kernel variant, or with run-time
- * lengths both ways, keep their shapes.
+ * may alias the inputs only if the inputs may be overwritten).  Task shapes
+ * decide how the work is split into blocks, never the arithmetic: with one
+ * schedule the results are bitwise the same for every shape.  The two
+ * schedules add the same terms in a different order, so their results differ
+ * by rounding (both within the mixed path's tolerance).  The call changes the
+ * plan: make it before the plan is shared between threads or solves are
+ * captured into a graph.  Plans running an opt-in kernel variant, or with
+ * run-time lengths both ways, keep their shapes.
  *   row_threads, col_threads  host, nullable: the shapes kept
+ *   (monc_proj_plan_schedule reports the schedule kept)
  * Errors: EINVAL for NULL plan, field or workspace pointers; the first failing
  * solve's status (the plan then keeps the shapes it had).
  */
@@ -475,6 +482,27 @@ int monc_proj_solve_krylov(monc_proj_plan_t plan, const void* u, const void* v, 
                            void* u_out, void* v_out, void* w_out, void* phi_out, void* workspace,
                            double tol, int max_iter, int precond, int* iterations, double* rel_residual,
                            void* stream);
+
+/*
+ * The plan's transform schedules: elements per thread of the compile-time
+ * row and column plans (the largest radix of a stage: 32 or 16 in FP32, 16
+ * in FP64) and the threads of a row task and of a column tile.  All outputs
+ * host, nullable.
+ */
+int monc_proj_plan_schedule(monc_proj_plan_t plan, int* row_elems, int* col_elems, int* row_threads,
+                            int* col_threads);
+
+/*
+ * Set the task shapes and column radix schedule of an FP32 mixed plan
+ * directly (for example one that monc_proj_autotune chose in an earlier run):
+ * row_threads 32, 64 or 128; col_threads 128, 256 or 512; col_elems 32, or
+ * 16 for square 256, 512 and 1024 grids with col_threads 256.  EINVAL for
+ * values outside those sets; EUNSUPPORTED for FP64 and refined plans, plans
+ * running an opt-in kernel variant, a run-time length whose shape would
+ * change, or a combination without kernels or shared memory (the plan then
+ * keeps what it had).  Same threading rule as monc_proj_autotune.
+ */
+int monc_proj_set_schedule(monc_proj_plan_t plan, int row_threads, int col_threads, int col_elems);
 
 /* Plan introspection: grid sizes, precision and the FP64-column count of a3. */
 int monc_proj_plan_info(monc_proj_plan_t plan, int* nx, int* ny, int* nz, int* precision,

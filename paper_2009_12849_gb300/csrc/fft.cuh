@@ -324,28 +324,33 @@ MP_HD constexpr int ct_stage_radix(int N, int NS, int E) {
     return 1;
 }
 
-template <typename R, int N, int NS> struct StageRadix {
-    static constexpr int value = ct_stage_radix(N, NS, ElemsPerThread<R>::value);
+// E (the elements a thread holds in a stage, which bounds the radix) is the
+// plan's radix schedule: the default is ElemsPerThread; a schedule with a
+// smaller E takes more, smaller stages (1024 = 32*32 with E = 32, 16*16*4
+// with E = 16) with fewer registers per thread.
+template <typename R> MP_HD constexpr int ept() { return ElemsPerThread<R>::value; }
+
+template <typename R, int N, int NS, int E = ept<R>()> struct StageRadix {
+    static constexpr int value = ct_stage_radix(N, NS, E);
 };
 
 // Position of the stage with the given Ns in the compile-time plan.
-template <typename R, int N> constexpr int stage_index_impl(int target) {
+template <int N, int E> constexpr int stage_index_impl(int target) {
     int ns = 1, s = 0;
     while (ns < target) {
-        ns *= ct_stage_radix(N, ns, ElemsPerThread<R>::value);
+        ns *= ct_stage_radix(N, ns, E);
         ++s;
     }
     return s;
 }
-template <typename R, int N, int NS> struct StageIndex {
-    static constexpr int value = stage_index_impl<R, N>(NS);
+template <typename R, int N, int NS, int E = ept<R>()> struct StageIndex {
+    static constexpr int value = stage_index_impl<N, E>(NS);
 };
 
-template <typename R, int N, int NS, int S, class Sc = BlockScope>
+template <typename R, int N, int NS, int S, class Sc = BlockScope, int E = ept<R>()>
 __device__ __forceinline__ void ct_stage(cplx<R>* buf, int nb, int bstride, const cplx<R>* __restrict__ tws) {
-    const cplx<R>* __restrict__ tw = tws + StageIndex<R, N, NS>::value * N;
-    constexpr int RAD = StageRadix<R, N, NS>::value;
-    constexpr int E = ElemsPerThread<R>::value;
+    const cplx<R>* __restrict__ tw = tws + StageIndex<R, N, NS, E>::value * N;
+    constexpr int RAD = StageRadix<R, N, NS, E>::value;
     constexpr int NB = (E + RAD - 1) / RAD;
     constexpr int NQ = N / RAD;
     const int total = NQ * nb;
@@ -389,13 +394,13 @@ __device__ __forceinline__ void ct_stage(cplx<R>* buf, int nb, int bstride, cons
     Sc::sync();
 }
 
-template <typename R, int N, int NS, int S, class Sc = BlockScope> struct CtFFT {
+template <typename R, int N, int NS, int S, class Sc = BlockScope, int E = ept<R>()> struct CtFFT {
     static __device__ __forceinline__ void run(cplx<R>* buf, int nb, int bstride, const cplx<R>* tw) {
-        ct_stage<R, N, NS, S, Sc>(buf, nb, bstride, tw);
-        CtFFT<R, N, NS * StageRadix<R, N, NS>::value, S, Sc>::run(buf, nb, bstride, tw);
+        ct_stage<R, N, NS, S, Sc, E>(buf, nb, bstride, tw);
+        CtFFT<R, N, NS * StageRadix<R, N, NS, E>::value, S, Sc, E>::run(buf, nb, bstride, tw);
     }
 };
-template <typename R, int N, int S, class Sc> struct CtFFT<R, N, N, S, Sc> {
+template <typename R, int N, int S, class Sc, int E> struct CtFFT<R, N, N, S, Sc, E> {
     static __device__ __forceinline__ void run(cplx<R>*, int, int, const cplx<R>*) {}
 };
 
@@ -410,17 +415,17 @@ template <typename R, int N, int S, class Sc> struct CtFFT<R, N, N, S, Sc> {
 // global elements are adjacent) or consecutive butterflies of one transform
 // (rows, whose elements are adjacent).
 // ---------------------------------------------------------------------------
-template <typename R, int N, int NS> struct StageInfo {
-    static constexpr int RAD = StageRadix<R, N, NS>::value;
+template <typename R, int N, int NS, int E = ept<R>()> struct StageInfo {
+    static constexpr int RAD = StageRadix<R, N, NS, E>::value;
     static constexpr int NQ = N / RAD;
     static constexpr int NEXT = NS * RAD;
     static constexpr bool LAST = (NEXT == N);
 };
 
-template <typename R, int N> constexpr int last_stage_ns_impl() {
+template <int N, int E> constexpr int last_stage_ns_impl() {
     int ns = 1;
     while (ns < N) {
-        const int rad = ct_stage_radix(N, ns, ElemsPerThread<R>::value);
+        const int rad = ct_stage_radix(N, ns, E);
         if (ns * rad == N) return ns;
         ns *= rad;
     }
@@ -428,8 +433,8 @@ template <typename R, int N> constexpr int last_stage_ns_impl() {
 }
 
 // Ns of the last stage of the compile-time plan for length N.
-template <typename R, int N> struct LastNs {
-    static constexpr int value = last_stage_ns_impl<R, N>();
+template <typename R, int N, int E = ept<R>()> struct LastNs {
+    static constexpr int value = last_stage_ns_impl<N, E>();
 };
 
 template <bool BFAST, int NQ>
@@ -440,11 +445,11 @@ __device__ __forceinline__ void bfly_map(int t, int nb, int& b, int& q) {
 
 // SYNC_IN: the inputs are read from the same shared buffer the stage writes,
 // so the block synchronises between the reads and the writes.
-template <typename R, int N, int S, bool BFAST, bool SYNC_IN = false, class Sc = BlockScope, class Load>
+template <typename R, int N, int S, bool BFAST, bool SYNC_IN = false, class Sc = BlockScope, int E = ept<R>(),
+          class Load>
 __device__ __forceinline__ void ct_first(cplx<R>* buf, int nb, int bstride, Load&& load) {
-    using SI = StageInfo<R, N, 1>;
+    using SI = StageInfo<R, N, 1, E>;
     constexpr int RAD = SI::RAD, NQ = SI::NQ;
-    constexpr int E = ElemsPerThread<R>::value;
     constexpr int NB = (E + RAD - 1) / RAD;
     const int total = NQ * nb;
     cplx<R> x[NB][RAD];
@@ -481,26 +486,26 @@ __device__ __forceinline__ void ct_first(cplx<R>* buf, int nb, int bstride, Load
     Sc::sync();
 }
 
-template <typename R, int N, int NS, int S, class Sc = BlockScope, bool STOP = StageInfo<R, N, NS>::LAST>
+template <typename R, int N, int NS, int S, class Sc = BlockScope, int E = ept<R>(),
+          bool STOP = StageInfo<R, N, NS, E>::LAST>
 struct CtMid {
     static __device__ __forceinline__ void run(cplx<R>* buf, int nb, int bstride, const cplx<R>* tw) {
-        ct_stage<R, N, NS, S, Sc>(buf, nb, bstride, tw);
-        CtMid<R, N, StageInfo<R, N, NS>::NEXT, S, Sc>::run(buf, nb, bstride, tw);
+        ct_stage<R, N, NS, S, Sc, E>(buf, nb, bstride, tw);
+        CtMid<R, N, StageInfo<R, N, NS, E>::NEXT, S, Sc, E>::run(buf, nb, bstride, tw);
     }
 };
-template <typename R, int N, int NS, int S, class Sc> struct CtMid<R, N, NS, S, Sc, true> {
+template <typename R, int N, int NS, int S, class Sc, int E> struct CtMid<R, N, NS, S, Sc, E, true> {
     static __device__ __forceinline__ void run(cplx<R>*, int, int, const cplx<R>*) {}
 };
 
-template <typename R, int N, int S, bool BFAST, class Sc = BlockScope, class Store>
+template <typename R, int N, int S, bool BFAST, class Sc = BlockScope, int E = ept<R>(), class Store>
 __device__ __forceinline__ void ct_last(const cplx<R>* buf, int nb, int bstride, const cplx<R>* __restrict__ tws,
                                         Store&& store) {
-    constexpr int NS = LastNs<R, N>::value;
-    const cplx<R>* __restrict__ tw = tws + StageIndex<R, N, NS>::value * N;
-    using SI = StageInfo<R, N, NS>;
+    constexpr int NS = LastNs<R, N, E>::value;
+    const cplx<R>* __restrict__ tw = tws + StageIndex<R, N, NS, E>::value * N;
+    using SI = StageInfo<R, N, NS, E>;
     static_assert(SI::LAST, "last stage");
     constexpr int RAD = SI::RAD, NQ = SI::NQ;
-    constexpr int E = ElemsPerThread<R>::value;
     constexpr int NB = (E + RAD - 1) / RAD;
     const int total = NQ * nb;
 #pragma unroll
@@ -532,15 +537,14 @@ __device__ __forceinline__ void ct_last(const cplx<R>* buf, int nb, int bstride,
 // of the thread before any butterfly is transformed, so loads it issues (the
 // operands of the store's read-modify-write) are all in flight at once
 // instead of one butterfly at a time; then store(b, q, x, NS, i) as ct_last.
-template <typename R, int N, int S, bool BFAST, class Sc = BlockScope, class Pre, class Store>
+template <typename R, int N, int S, bool BFAST, class Sc = BlockScope, int E = ept<R>(), class Pre, class Store>
 __device__ __forceinline__ void ct_last_pre(const cplx<R>* buf, int nb, int bstride, const cplx<R>* __restrict__ tws,
                                             Pre&& pre, Store&& store) {
-    constexpr int NS = LastNs<R, N>::value;
-    const cplx<R>* __restrict__ tw = tws + StageIndex<R, N, NS>::value * N;
-    using SI = StageInfo<R, N, NS>;
+    constexpr int NS = LastNs<R, N, E>::value;
+    const cplx<R>* __restrict__ tw = tws + StageIndex<R, N, NS, E>::value * N;
+    using SI = StageInfo<R, N, NS, E>;
     static_assert(SI::LAST, "last stage");
     constexpr int RAD = SI::RAD, NQ = SI::NQ;
-    constexpr int E = ElemsPerThread<R>::value;
     constexpr int NB = (E + RAD - 1) / RAD;
     const int total = NQ * nb;
 #pragma unroll
@@ -579,15 +583,14 @@ __device__ __forceinline__ void ct_last_pre(const cplx<R>* buf, int nb, int bstr
 // Last stage for an output buffer that aliases the input: every thread
 // computes its butterflies into registers, the block synchronises, then the
 // results go to store(b, q, x, NS).
-template <typename R, int N, int S, bool BFAST, class Sc = BlockScope, class Store>
+template <typename R, int N, int S, bool BFAST, class Sc = BlockScope, int E = ept<R>(), class Store>
 __device__ __forceinline__ void ct_last_sync(const cplx<R>* buf, int nb, int bstride, const cplx<R>* __restrict__ tws,
                                              Store&& store) {
-    constexpr int NS = LastNs<R, N>::value;
-    const cplx<R>* __restrict__ tw = tws + StageIndex<R, N, NS>::value * N;
-    using SI = StageInfo<R, N, NS>;
+    constexpr int NS = LastNs<R, N, E>::value;
+    const cplx<R>* __restrict__ tw = tws + StageIndex<R, N, NS, E>::value * N;
+    using SI = StageInfo<R, N, NS, E>;
     static_assert(SI::LAST, "last stage");
     constexpr int RAD = SI::RAD, NQ = SI::NQ;
-    constexpr int E = ElemsPerThread<R>::value;
     constexpr int NB = (E + RAD - 1) / RAD;
     const int total = NQ * nb;
     cplx<R> x[NB][RAD];

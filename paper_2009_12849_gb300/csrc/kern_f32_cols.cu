@@ -15,13 +15,18 @@ template <> KernelFn pick_k_inv_cols<float>(int n) {
 template <> KernelFn pick_fwd_cols_persist<float>(int n) { MP_PICK_F32(k_cols_persist, nullptr, , false) }
 template <> KernelFn pick_inv_cols_persist<float>(int n) { MP_PICK_F32(k_cols_persist, nullptr, , true) }
 template <> KernelFn pick_tridiag<float>() { return k_tridiag<float>; }
-KernelFn pick_cols_square_f32(int ny, int nxp, int tw, int bs, bool inv) {
-#define MP_SQ(N, NXP, TW)                                                                    \
-    if (ny == N && nxp == NXP && tw == TW && bs == ColPitch<N>::value)                      \
-        return inv ? (KernelFn)k_inv_cols<float, N, false, NXP, TW> : (KernelFn)k_fwd_cols<float, N, NXP, TW>;
-    MP_SQ(1024, 516, 8)
-    MP_SQ(512, 260, 16)
-    MP_SQ(256, 132, 32)
+KernelFn pick_cols_square_f32(int ny, int nxp, int tw, int bs, bool inv, int e) {
+#define MP_SQ(N, NXP, TW, E)                                                                           \
+    if (ny == N && nxp == NXP && tw == TW && e == E && bs == ColPitch<N>::value)                      \
+        return inv ? (KernelFn)k_inv_cols<float, N, false, NXP, TW, E> : (KernelFn)k_fwd_cols<float, N, NXP, TW, E>;
+    // the default schedule (E = 32) with the default tiles (256 threads)
+    MP_SQ(1024, 516, 8, 32)
+    MP_SQ(512, 260, 16, 32)
+    MP_SQ(256, 132, 32, 32)
+    // the E = 16 schedule with 256-thread tiles
+    MP_SQ(1024, 516, 4, 16)
+    MP_SQ(512, 260, 8, 16)
+    MP_SQ(256, 132, 16, 16)
 #undef MP_SQ
     return nullptr;
 }

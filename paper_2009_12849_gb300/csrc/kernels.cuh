@@ -17,6 +17,7 @@ struct ProjParams {
     FftFactors fx, fy;
     const void* twx;            // per-stage twiddle tables of the x plan (storage precision)
     const void* twy;            // per-stage twiddle tables of the y plan
+    const void* twy16;          // the same for the E = 16 radix schedule (FP32 square grids; else null)
     const double* svol;         // [nz]   rho_c[k] dz[k]
     const double* rflo;         // [nz]   rho_f[k]   (0 at k = 0)
     const double* rfhi;         // [nz]   rho_f[k+1] (0 at k = nz-1)
@@ -384,7 +385,7 @@ __device__ __forceinline__ void discard_fwd_tile(const ProjParams& p, int k, int
 
 // One column task of a compile-time length: tile `tile` of level k, T -> S.
 // NXP and TW as in inv_cols_ct_task.
-template <typename R, int NY, int NXP = 0, int TW = 0>
+template <typename R, int NY, int NXP = 0, int TW = 0, int E = ept<R>()>
 __device__ __forceinline__ void fwd_cols_task(const ProjParams& p, unsigned char* smem_raw, int k, int tile) {
     using C = cplx<R>;
     const int nxh = p.nxh;
@@ -398,20 +399,21 @@ __device__ __forceinline__ void fwd_cols_task(const ProjParams& p, unsigned char
     auto load = [&](int c, int j) -> C {
         return (kx0 + c < nxh) ? T[j * nxp + c] : cmk<R>((R)0, (R)0);
     };
-    ct_first<R, NY, -1, true>(buf, tw, bs, load);
+    const C* twy = ctab<R>(E == ept<R>() ? p.twy : p.twy16);
+    ct_first<R, NY, -1, true, false, BlockScope, E>(buf, tw, bs, load);
     if (p.ho.discard) discard_fwd_tile<R>(p, k, tile);
-    CtMid<R, NY, StageInfo<R, NY, 1>::NEXT, -1>::run(buf, tw, bs, ctab<R>(p.twy));
+    CtMid<R, NY, StageInfo<R, NY, 1, E>::NEXT, -1, BlockScope, E>::run(buf, tw, bs, twy);
     auto store = [&](int c, int q, const C* x, int ns) {
         if (kx0 + c >= nxh) return;
-        constexpr int RAD = StageInfo<R, NY, LastNs<R, NY>::value>::RAD;
+        constexpr int RAD = StageInfo<R, NY, LastNs<R, NY, E>::value, E>::RAD;
         C* d = S + q * nxp + c;
 #pragma unroll
         for (int r = 0; r < RAD; ++r) d[r * ns * nxp] = x[r];
     };
-    ct_last<R, NY, -1, true>(buf, tw, bs, ctab<R>(p.twy), store);
+    ct_last<R, NY, -1, true, BlockScope, E>(buf, tw, bs, twy, store);
 }
 
-template <typename R, int NY, int NXP = 0, int TW = 0>
+template <typename R, int NY, int NXP = 0, int TW = 0, int E = ept<R>()>
 __global__ void __launch_bounds__(512) k_fwd_cols(ProjParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using C = cplx<R>;
@@ -419,7 +421,7 @@ __global__ void __launch_bounds__(512) k_fwd_cols(ProjParams p) {
     const int k = kl;
     const int tile = blockIdx.x - kl * p.ntiles;
     if constexpr (NY > 0) {
-        fwd_cols_task<R, NY, NXP, TW>(p, smem_raw, k, tile);
+        fwd_cols_task<R, NY, NXP, TW, E>(p, smem_raw, k, tile);
     } else {
         C* buf = (C*)smem_raw;
         load_cols<R>(buf, (const C*)p.T, k, tile * p.tw_cols, p, nullptr);
@@ -756,7 +758,7 @@ __device__ __forceinline__ InvColField<R> inv_col_field(const ProjParams& p, int
 // spectral row pitch and the tile width known at compile time (square grids
 // with the default tiles), which turns the element addresses into constant
 // offsets from one per-thread pointer.
-template <typename R, int NY, int F, int NXP = 0, int TW = 0>
+template <typename R, int NY, int F, int NXP = 0, int TW = 0, int E = ept<R>()>
 __device__ __forceinline__ void inv_cols_ct_task(const ProjParams& p, int k, int kx0, cplx<R>* buf) {
     using C = cplx<R>;
     const int nxh = p.nxh;
@@ -771,13 +773,14 @@ __device__ __forceinline__ void inv_cols_ct_task(const ProjParams& p, int k, int
         if constexpr (F == 1) return cmul(v, ey[j]);
         else return v;
     };
-    ct_first<R, NY, 1, true>(buf, tw, bs, load);
-    CtMid<R, NY, StageInfo<R, NY, 1>::NEXT, 1>::run(buf, tw, bs, ctab<R>(p.twy));
+    const C* twy = ctab<R>(E == ept<R>() ? p.twy : p.twy16);
+    ct_first<R, NY, 1, true, false, BlockScope, E>(buf, tw, bs, load);
+    CtMid<R, NY, StageInfo<R, NY, 1, E>::NEXT, 1, BlockScope, E>::run(buf, tw, bs, twy);
     const C* ex = ctab<R>(p.ex);
     C* dst = (F == 0 ? (C*)p.Tp : F == 1 ? (C*)p.Tgy : F == 2 ? (C*)p.Tgz : (C*)p.Tphi) + (size_t)k * NY * nxp + kx0;
     auto store = [&](int c, int q, const C* x, int ns) {
         if (kx0 + c >= nxh) return;
-        constexpr int RAD = StageInfo<R, NY, LastNs<R, NY>::value>::RAD;
+        constexpr int RAD = StageInfo<R, NY, LastNs<R, NY, E>::value, E>::RAD;
         C* d = dst + q * nxp + c;
         if constexpr (F == 0) {
             const C e = ex[kx0 + c];
@@ -788,34 +791,34 @@ __device__ __forceinline__ void inv_cols_ct_task(const ProjParams& p, int k, int
             for (int r = 0; r < RAD; ++r) d[r * ns * nxp] = x[r];
         }
     };
-    ct_last<R, NY, 1, true>(buf, tw, bs, ctab<R>(p.twy), store);
+    ct_last<R, NY, 1, true, BlockScope, E>(buf, tw, bs, twy, store);
 }
 
 // One column task of a compile-time length: tile from kx0 of level k; kind
 // 0 transforms the p^ tile (x- and y-gradient, and phi if requested; with
 // PHI the potential alone), kind 1 the gz^ tile.
-template <typename R, int NY, bool PHI, int NXP = 0, int TW = 0>
+template <typename R, int NY, bool PHI, int NXP = 0, int TW = 0, int E = ept<R>()>
 __device__ __forceinline__ void inv_cols_tile(const ProjParams& p, unsigned char* smem_raw, int k, int kx0,
                                               int kind) {
     cplx<R>* buf = (cplx<R>*)smem_raw;
     if constexpr (PHI) {
-        if (kind == 0) inv_cols_ct_task<R, NY, 3, NXP, TW>(p, k, kx0, buf);
+        if (kind == 0) inv_cols_ct_task<R, NY, 3, NXP, TW, E>(p, k, kx0, buf);
     } else if (kind == 0) {
-        inv_cols_ct_task<R, NY, 0, NXP, TW>(p, k, kx0, buf);
+        inv_cols_ct_task<R, NY, 0, NXP, TW, E>(p, k, kx0, buf);
         __syncthreads();
-        inv_cols_ct_task<R, NY, 1, NXP, TW>(p, k, kx0, buf);
+        inv_cols_ct_task<R, NY, 1, NXP, TW, E>(p, k, kx0, buf);
         if (p.nch == 4) {
             __syncthreads();
-            inv_cols_ct_task<R, NY, 3, NXP, TW>(p, k, kx0, buf);
+            inv_cols_ct_task<R, NY, 3, NXP, TW, E>(p, k, kx0, buf);
         }
     } else if (p.kbase + k > 0) {
-        inv_cols_ct_task<R, NY, 2, NXP, TW>(p, k, kx0, buf);
+        inv_cols_ct_task<R, NY, 2, NXP, TW, E>(p, k, kx0, buf);
     }
 }
 
 // PHI: the potential alone (refinement passes): kind 0 transforms the p^ tile
 // into Tphi, kind 1 does nothing.
-template <typename R, int NY, bool PHI = false, int NXP = 0, int TW = 0>
+template <typename R, int NY, bool PHI = false, int NXP = 0, int TW = 0, int E = ept<R>()>
 __global__ void __launch_bounds__(512) k_inv_cols(ProjParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using C = cplx<R>;
@@ -823,7 +826,7 @@ __global__ void __launch_bounds__(512) k_inv_cols(ProjParams p) {
         const int task = blockIdx.x >> 1;
         const int kl = task / p.ntiles;
         const int tw = TW ? TW : p.tw_cols;
-        inv_cols_tile<R, NY, PHI, NXP, TW>(p, smem_raw, kl, (task - kl * p.ntiles) * tw, blockIdx.x & 1);
+        inv_cols_tile<R, NY, PHI, NXP, TW, E>(p, smem_raw, kl, (task - kl * p.ntiles) * tw, blockIdx.x & 1);
         return;
     }
     const int nf = p.nch;

@@ -33,6 +33,7 @@ struct monc_proj_plan_s {
     // device tables (one allocation)
     void* dev_tables;
     const void* twx; const void* twy;
+    const void* twy16;                    // y twiddles of the E = 16 schedule (FP32, ny = 256/512/1024), or null
     const double* svol; const double* rflo; const double* rfhi;
     const double* acoef; const double* idzn; const double* csum;
     const float* svol32; const float* acoef32; const float* csum32; const float* idzn32;
@@ -52,6 +53,7 @@ struct monc_proj_plan_s {
     bool ct_cols;                         // compile-time length along y
     bool fused;                           // square compile-time grid: fused persistent kernels
     int row_threads, col_threads;         // threads of a compile-time row task / column tile
+    int col_e;                            // radix schedule of the compile-time column plans (elements per thread)
     int refine_passes;                    // MONC_PROJ_REFINED: passes per solve
     bool tma_cols;                        // FP32 compile-time column lengths: TMA-staged column kernels
     size_t smem_tma;                      // their dynamic shared memory (two tile buffers)
@@ -301,7 +303,7 @@ ProjParams make_params(const monc_proj_plan_s* p, const void* u, const void* v, 
     ProjParams q{};
     q.nx = p->nx; q.ny = p->ny; q.nz = p->nz; q.nxh = p->nxh; q.nxp = p->nxp;
     q.fx = p->fx; q.fy = p->fy;
-    q.twx = p->twx; q.twy = p->twy;
+    q.twx = p->twx; q.twy = p->twy; q.twy16 = p->twy16;
     q.svol = p->svol; q.rflo = p->rflo; q.rfhi = p->rfhi; q.acoef = p->acoef; q.idzn = p->idzn;
     q.csum = p->csum; q.svol32 = p->svol32; q.acoef32 = p->acoef32; q.csum32 = p->csum32;
     q.rflo32 = p->rflo32; q.rfhi32 = p->rfhi32;
@@ -360,9 +362,9 @@ template <typename R> SolveKernels pick_kernels(const monc_proj_plan_s* p) {
                         : p->persist_cols ? pick_inv_cols_persist<R>(ny) : pick_k_inv_cols<R>(ny),
                     ref ? pick_refined_inv_rows(nx) : pick_k_inv_rows<R>(nx)};
     if (sizeof(R) == 4) {
-        if (KernelFn f = pick_cols_square_f32(ny, p->nxp, p->tw_cols, p->bs_col, false)) ks.fwd_cols = f;
+        if (KernelFn f = pick_cols_square_f32(ny, p->nxp, p->tw_cols, p->bs_col, false, p->col_e)) ks.fwd_cols = f;
         if (!ref && !p->persist_cols)
-            if (KernelFn f = pick_cols_square_f32(ny, p->nxp, p->tw_cols, p->bs_col, true)) ks.inv_cols = f;
+            if (KernelFn f = pick_cols_square_f32(ny, p->nxp, p->tw_cols, p->bs_col, true, p->col_e)) ks.inv_cols = f;
     }
     return ks;
 }
@@ -682,7 +684,7 @@ int validate_grid(int nx, int ny, int nz, double dx, double dy, const double* dz
 
 // Offsets of the plan's device tables inside one contiguous blob.
 struct TableOffsets {
-    size_t twx, twy, sv, rl, rh, a, iz, cs, sv32, a32, cs32, iz32, rl32, rh32, lx, ly, ex, ey, err;
+    size_t twx, twy, twy16, sv, rl, rh, a, iz, cs, sv32, a32, cs32, iz32, rl32, rh32, lx, ly, ex, ey, err;
 };
 
 // Fill the host-side part of a plan (sizes, radix plans, task shapes,
@@ -700,6 +702,7 @@ void set_task_shapes(monc_proj_plan_s* p) {
     const size_t csz = fp64 ? 16 : 8;
     const bool ctx = p->ct_rows, cty = p->ct_cols;
     const int E = fp64 ? kMaxRadixF64 : kMaxRadixF32;
+    const int Ec = fp64 ? kMaxRadixF64 : p->col_e;      // the column plans' schedule
     p->bs_row = spad_len(nx);
     // column tiles: a pitch of 4 (mod 16) complex elements spreads the
     // columns of a tile over distinct shared-memory banks
@@ -713,12 +716,12 @@ void set_task_shapes(monc_proj_plan_s* p) {
     p->nrb_fwd = (ny + p->rows_fwd - 1) / p->rows_fwd;
     p->thr_fwd_rows = ctx ? threads_for(npair * nx, E) : 256;
     p->smem_fwd_rows = (size_t)(ctx ? 1 : 2) * npair * p->bs_row * csz;
-    int tw = cty ? std::max(1, std::min(32, p->col_threads * E / ny))
+    int tw = cty ? std::max(1, std::min(32, p->col_threads * Ec / ny))
                  : (int)std::max<size_t>(1, std::min<size_t>(8, budget / (2 * (size_t)p->bs_col * csz)));
     tw = std::min(tw, p->nxh);
     p->tw_cols = tw;
     p->ntiles = (p->nxh + tw - 1) / tw;
-    p->thr_cols = cty ? threads_for(tw * ny, E) : 256;
+    p->thr_cols = cty ? threads_for(tw * ny, Ec) : 256;
     p->smem_cols = (size_t)(cty ? 1 : 2) * tw * p->bs_col * csz;
     p->smem_fcols = p->smem_cols;
     // inverse row tasks: pairs of rows, one complex transform per channel and
@@ -834,6 +837,15 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     to.twy = blob.size();
     if (fp64) push_complex<double>(blob, tsyr, tsyi); else push_complex<float>(blob, tsyr, tsyi);
     pad_blob(blob);
+    // the E = 16 schedule of the y plan (FP32 square-grid column kernels)
+    to.twy16 = 0;
+    if (!fp64 && cty && (ny == 256 || ny == 512 || ny == 1024)) {
+        std::vector<double> t16r, t16i;
+        stage_tables(factorize(ny, 16, true), t16r, t16i);
+        to.twy16 = blob.size();
+        push_complex<float>(blob, t16r, t16i);
+        pad_blob(blob);
+    }
     to.sv = blob.size(); push_doubles(blob, svol); pad_blob(blob);
     to.rl = blob.size(); push_doubles(blob, rflo); pad_blob(blob);
     to.rh = blob.size(); push_doubles(blob, rfhi); pad_blob(blob);
@@ -860,6 +872,7 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     p->ct_rows = ctx;
     p->ct_cols = cty;
     p->row_threads = kRowTaskThreads;
+    p->col_e = kMaxRadixF32;
     p->col_threads = kColTaskThreads;
     set_task_shapes(p);
     const int npair = p->rows_fwd / 2;
@@ -941,6 +954,7 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
 // Point the plan's table pointers into device memory `db` holding the blob.
 void plan_bind(monc_proj_plan_s* p, unsigned char* db, const TableOffsets& to) {
     p->twx = db + to.twx; p->twy = db + to.twy;
+    p->twy16 = to.twy16 ? db + to.twy16 : nullptr;
     p->svol = (const double*)(db + to.sv); p->rflo = (const double*)(db + to.rl);
     p->rfhi = (const double*)(db + to.rh); p->acoef = (const double*)(db + to.a);
     p->idzn = (const double*)(db + to.iz); p->lamx = (const double*)(db + to.lx);
@@ -1397,7 +1411,7 @@ int monc_proj_solve_batch(const monc_proj_plan_t* plans, const monc_proj_fields*
 namespace {
 // Plans whose solve is the default FP32 split kernels of compile-time lengths
 bool group_eligible(const monc_proj_plan_s* p) {
-    return p->precision == MONC_PROJ_MIXED && p->ct_rows && p->ct_cols && !p->fused && !p->pipe &&
+    return p->precision == MONC_PROJ_MIXED && p->ct_rows && p->ct_cols && p->col_e == kMaxRadixF32 && !p->fused && !p->pipe &&
            !p->persist_cols && !p->tma_cols && !p->tc_cols && pick_group_f32(0, p->nx) && pick_group_f32(1, p->ny);
 }
 
@@ -1598,12 +1612,18 @@ bool shapes_fit(const monc_proj_plan_s* p) {
     return p->thr_fwd_rows <= 512 && p->thr_cols <= 512 && p->thr_inv_rows[0] <= 512 && p->thr_inv_rows[1] <= 512 &&
            p->smem_fwd_rows <= lim && p->smem_cols <= lim && p->smem_inv_rows[0] <= lim && p->smem_inv_rows[1] <= lim;
 }
-int apply_shapes(monc_proj_plan_s* p, int rt, int ct) {
+// Task shapes and column radix schedule e (32, or 16 where the square-grid
+// kernels of that schedule exist).
+int apply_shapes(monc_proj_plan_s* p, int rt, int ct, int e) {
     p->row_threads = rt;
     p->col_threads = ct;
+    p->col_e = e;
     set_task_shapes(p);
     p->smem_fcols = p->smem_cols;
     if (!shapes_fit(p)) return MONC_PROJ_EUNSUPPORTED;
+    if (e != kMaxRadixF32 && (p->precision != MONC_PROJ_MIXED || !p->twy16 ||
+                              !pick_cols_square_f32(p->ny, p->nxp, p->tw_cols, p->bs_col, false, e)))
+        return MONC_PROJ_EUNSUPPORTED;
     return p->precision == MONC_PROJ_FP64 ? set_kernel_attrs<double>(p) : set_kernel_attrs<float>(p);
 }
 }  // namespace
@@ -1612,7 +1632,7 @@ int monc_proj_autotune(monc_proj_plan_t plan, const void* u, const void* v, cons
                        void* v_out, void* w_out, void* workspace, int reps, void* stream, int* row_threads,
                        int* col_threads) {
     if (!plan || !u || !v || !w || !u_out || !v_out || !w_out || !workspace) return MONC_PROJ_EINVAL;
-    const int r0 = plan->row_threads, c0 = plan->col_threads;
+    const int r0 = plan->row_threads, c0 = plan->col_threads, e0s = plan->col_e;
     auto report = [&](int rc) {
         if (row_threads) *row_threads = plan->row_threads;
         if (col_threads) *col_threads = plan->col_threads;
@@ -1629,17 +1649,19 @@ int monc_proj_autotune(monc_proj_plan_t plan, const void* u, const void* v, cons
         return report(MONC_PROJ_ECUDA);
     }
     const int rts[] = {32, 64, 128};
-    const int cts[] = {128, 256, 512};
+    // column candidates: (threads per tile, radix schedule)
+    const std::pair<int, int> cts[] = {{128, 32}, {256, 32}, {512, 32}, {256, 16}};
     float best = INFINITY;
-    int br = r0, bc = c0;
+    int br = r0, bc = c0, be = e0s;
     int rc = MONC_PROJ_OK;
-    std::vector<std::pair<int, int>> seen;      // (rows per forward task, columns per tile) tried
+    std::vector<std::vector<int>> seen;      // (rows per forward task, columns per tile, schedule) tried
     for (int rt : rts) {
         if (!plan->ct_rows && rt != r0) continue;
-        for (int ct : cts) {
-            if (!plan->ct_cols && ct != c0) continue;
-            if (apply_shapes(plan, rt, ct) != MONC_PROJ_OK) continue;
-            const std::pair<int, int> key(plan->rows_fwd, plan->tw_cols);
+        for (const auto& cte : cts) {
+            const int ct = cte.first, ce = cte.second;
+            if (!plan->ct_cols && (ct != c0 || ce != e0s)) continue;
+            if (apply_shapes(plan, rt, ct, ce) != MONC_PROJ_OK) continue;
+            const std::vector<int> key{plan->rows_fwd, plan->tw_cols, plan->col_e};
             if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
             seen.push_back(key);
             rc = monc_proj_solve(plan, u, v, w, u_out, v_out, w_out, nullptr, workspace, stream);
@@ -1658,6 +1680,7 @@ int monc_proj_autotune(monc_proj_plan_t plan, const void* u, const void* v, cons
                 best = ms;
                 br = rt;
                 bc = ct;
+                be = ce;
             }
         }
         if (rc != MONC_PROJ_OK) break;
@@ -1665,8 +1688,41 @@ int monc_proj_autotune(monc_proj_plan_t plan, const void* u, const void* v, cons
     cudaGetLastError();
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    const int ra = apply_shapes(plan, rc == MONC_PROJ_OK ? br : r0, rc == MONC_PROJ_OK ? bc : c0);
+    const bool ok = rc == MONC_PROJ_OK;
+    const int ra = apply_shapes(plan, ok ? br : r0, ok ? bc : c0, ok ? be : e0s);
     return report(rc != MONC_PROJ_OK ? rc : ra);
+}
+
+int monc_proj_set_schedule(monc_proj_plan_t plan, int row_threads, int col_threads, int col_elems) {
+    if (!plan) return MONC_PROJ_EINVAL;
+    if (plan->fused || plan->persist_cols || plan->tma_cols || plan->pipe || plan->tc_cols ||
+        plan->precision == MONC_PROJ_FP64 || plan->precision == MONC_PROJ_REFINED)
+        return MONC_PROJ_EUNSUPPORTED;
+    const bool shape_ok = (row_threads == 32 || row_threads == 64 || row_threads == 128) &&
+                          (col_threads == 128 || col_threads == 256 || col_threads == 512) &&
+                          (col_elems == 32 || col_elems == 16);
+    if (!shape_ok) return MONC_PROJ_EINVAL;
+    if ((!plan->ct_rows && row_threads != plan->row_threads) ||
+        (!plan->ct_cols && (col_threads != plan->col_threads || col_elems != plan->col_e)))
+        return MONC_PROJ_EUNSUPPORTED;
+    const int r0 = plan->row_threads, c0 = plan->col_threads, e0 = plan->col_e;
+    const int rc = apply_shapes(plan, row_threads, col_threads, col_elems);
+    if (rc != MONC_PROJ_OK) {
+        apply_shapes(plan, r0, c0, e0);
+        return rc;
+    }
+    return MONC_PROJ_OK;
+}
+
+int monc_proj_plan_schedule(monc_proj_plan_t plan, int* row_elems, int* col_elems, int* row_threads,
+                            int* col_threads) {
+    if (!plan) return MONC_PROJ_EINVAL;
+    const bool fp64 = plan->precision == MONC_PROJ_FP64;
+    if (row_elems) *row_elems = fp64 ? kMaxRadixF64 : kMaxRadixF32;
+    if (col_elems) *col_elems = fp64 ? kMaxRadixF64 : plan->col_e;
+    if (row_threads) *row_threads = plan->row_threads;
+    if (col_threads) *col_threads = plan->col_threads;
+    return MONC_PROJ_OK;
 }
 
 int monc_proj_plan_info(monc_proj_plan_t plan, int* nx, int* ny, int* nz, int* precision,

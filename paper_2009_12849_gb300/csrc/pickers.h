@@ -22,9 +22,10 @@ template <typename R> KernelFn pick_inv_cols_persist(int n);
 template <typename R> KernelFn pick_fwd_fused(int n);
 template <typename R> KernelFn pick_inv_fused(int n);
 template <typename R> KernelFn pick_tridiag();
-// FP32 column kernels with the spectral pitch and tile width fixed at compile
-// time (nx = ny = 256, 512, 1024 with the default tiles); nullptr otherwise
-KernelFn pick_cols_square_f32(int ny, int nxp, int tw, int bs, bool inv);
+// FP32 column kernels with the spectral pitch, tile width and radix schedule
+// (e: elements per thread, 32 or 16) fixed at compile time (nx = ny = 256,
+// 512, 1024 with 256-thread tiles); nullptr otherwise
+KernelFn pick_cols_square_f32(int ny, int nxp, int tw, int bs, bool inv, int e);
 // grouped-launch kernels of batched FP32 projections (group.cuh): phase 0..4
 // = forward rows, forward columns, vertical solve, inverse columns, inverse
 // rows, for length n (the rows' nx or the columns' ny; any n for phase 2);

@@ -51,6 +51,7 @@ EXPORTS = [
     "monc_proj_krylov_workspace_size", "monc_proj_solve_krylov", "monc_proj_set_allocator",
     "monc_proj_spectral_pitch", "monc_proj_forward_slab", "monc_proj_vertical_pencil", "monc_proj_inverse_slab",
     "monc_proj_pack_pencils", "monc_proj_unpack_pencils", "monc_proj_solve_batch_grouped",
+    "monc_proj_plan_schedule", "monc_proj_set_schedule",
 ]
 
 # Allocator hooks of plan tables (monc_proj_set_allocator)
@@ -90,6 +91,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.monc_proj_batch_workspace_size.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(sz)]
     L.monc_proj_solve_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Fields), i, vp, sz, vp]
     L.monc_proj_solve_batch_grouped.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Fields), i, vp, sz, vp]
+    L.monc_proj_set_schedule.argtypes = [vp, i, i, i]
     L.monc_proj_sync_status.argtypes = [vp, vp]
     L.monc_proj_destroy.argtypes = [vp]
     L.monc_proj_status_string.argtypes = [i]
@@ -111,6 +113,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.monc_proj_spectral_pitch.argtypes = [vp, ip]
     L.monc_proj_forward_slab.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp]
     L.monc_proj_vertical_pencil.argtypes = [vp, i, i, vp, vp, vp, vp]
+    L.monc_proj_plan_schedule.argtypes = [vp, ip, ip, ip, ip]
     L.monc_proj_inverse_slab.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.monc_proj_pack_pencils.argtypes = [vp, i, i, vp, vp, vp]
     L.monc_proj_unpack_pencils.argtypes = [vp, i, i, vp, vp, vp]
@@ -274,6 +277,21 @@ def monc_proj_plan_info(plan: int) -> dict:
                                               *[ctypes.byref(x) for x in lls]), "monc_proj_plan_info")
     return {"nx": ints[0].value, "ny": ints[1].value, "nz": ints[2].value,
             "precision": ints[3].value, "fp64_columns": lls[0].value, "total_columns": lls[1].value}
+
+
+def monc_proj_plan_schedule(plan: int) -> dict:
+    """Elements per thread (radix schedule) of the row and column plans and
+    the task shapes."""
+    vals = [ctypes.c_int() for _ in range(4)]
+    _check(load_library().monc_proj_plan_schedule(ctypes.c_void_p(plan), *[ctypes.byref(v) for v in vals]),
+           "monc_proj_plan_schedule")
+    return dict(zip(("row_elems", "col_elems", "row_threads", "col_threads"), (v.value for v in vals)))
+
+
+def monc_proj_set_schedule(plan: int, row_threads: int, col_threads: int, col_elems: int):
+    """Set the task shapes and column radix schedule of an FP32 mixed plan."""
+    _check(load_library().monc_proj_set_schedule(ctypes.c_void_p(plan), int(row_threads), int(col_threads),
+                                                 int(col_elems)), "monc_proj_set_schedule")
 
 
 def monc_proj_profile(plan: int, enable: bool):

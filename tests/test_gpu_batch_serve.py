@@ -185,6 +185,56 @@ def test_autotune_keeps_results_bitwise(shape):
     P.close()
 
 
+@pytest.mark.parametrize("n,nz", [(256, 12), (512, 6), (1024, 3)])
+def test_radix_schedules_match_the_oracle(n, nz):
+    """The column transforms' E = 16 schedule (1024 = 16*16*4) against the FP64
+    oracle at the mixed tolerance, with and without phi; the autotuner keeps
+    one of the candidates and, when it keeps the default schedule, results
+    bitwise equal to the untuned plan's."""
+    import torch
+    import oracle as O
+    mp = _mp()
+    g = W.make_grid(n, n, nz, 25.0, 20.0, W.geometric_dz(nz, 10.0, 100.0))
+    dev = torch.device("cuda", 0)
+    u, v, w = W.random_fields(g, 12, True)
+    u, v, w = (a.astype(np.float32).astype(np.float64) for a in (u, v, w))
+    ref = O.project(u, v, w, g.dx, g.dy, g.dz, g.rho_c, g.rho_f)
+    tu, tv, tw = (torch.tensor(a, dtype=torch.float32, device=dev) for a in (u, v, w))
+    P = mp.Projector.from_grid(g, "mixed", dev)
+    assert mp.monc_proj_plan_schedule(P.plan)["col_elems"] == 32
+    base = [x.clone() for x in P.solve(tu, tv, tw, phi=True)]
+    mp.monc_proj_set_schedule(P.plan, 128, 256, 16)
+    sch = mp.monc_proj_plan_schedule(P.plan)
+    assert sch["col_elems"] == 16 and sch["col_threads"] == 256
+    got = P.solve(tu, tv, tw, phi=True)
+    torch.cuda.synchronize()
+    assert P.sync_status() == 0
+    num = sum(np.linalg.norm(a.double().cpu().numpy() - b) ** 2 for a, b in zip(got[:3], ref[:3]))
+    den = sum(np.linalg.norm(b) ** 2 for b in ref[:3])
+    assert (num / den) ** 0.5 < 1e-5
+    div = O.divergence_residual(*(a.double().cpu().numpy() for a in got[:3]), u, v, w, g.dx, g.dy, g.dz,
+                                g.rho_c, g.rho_f)
+    assert div < 1e-6
+    assert not all(torch.equal(a, b) for a, b in zip(base, got))     # a different summation order
+    with pytest.raises(mp.ProjError):
+        mp.monc_proj_set_schedule(P.plan, 128, 512, 16)              # no kernels for that tile
+    assert mp.monc_proj_plan_schedule(P.plan)["col_elems"] == 16    # kept on refusal
+    mp.monc_proj_set_schedule(P.plan, 128, 256, 32)
+    again = P.solve(tu, tv, tw, phi=True)
+    torch.cuda.synchronize()
+    for a, b in zip(base, again):
+        assert torch.equal(a, b)
+    rt, ct = P.autotune(tu, tv, tw, reps=2)
+    sch = mp.monc_proj_plan_schedule(P.plan)
+    assert (ct, sch["col_elems"]) in ((128, 32), (256, 32), (512, 32), (256, 16))
+    tuned = P.solve(tu, tv, tw, phi=True)
+    torch.cuda.synchronize()
+    if sch["col_elems"] == 32:
+        for a, b in zip(base, tuned):
+            assert torch.equal(a, b)
+    P.close()
+
+
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_host_buffer_solve_matches_device_solve(prec):
     """monc_proj_solve_host (host arrays in and out through a device staging
