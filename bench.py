@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -181,6 +182,20 @@ def path_bytes_per_point(elem: int) -> float:
     FP32).  The spectral w-gradient the mixed path also writes and reads is
     not counted, nor any hand-off between the passes of a 2D transform."""
     return 13.0 * elem
+
+
+# Dense FP64 arithmetic rate of one GB300 (nominal; the FP64 path is bound by it)
+FP64_PEAK_TFLOPS = 1.25
+
+
+def fp64_flops_per_point(nx, ny):
+    """Algorithmic FP64 flops per grid point of one projection: the forward
+    real 2D transform and the three inverse real 2D transforms at 5 n log2 n per
+    complex transform of n points (a real transform of n points as half of one:
+    2.5 log2(nx ny) per point each, 10 log2(nx ny) for the four), the vertical
+    solve at 21 flops per complex column and level over nx/2 + 1 of nx columns
+    (11 per point), the divergence (10) and the correction (3)."""
+    return 10.0 * math.log2(nx * ny) + 24.0
 
 
 def recorded_path_traffic():
@@ -438,6 +453,11 @@ def main():
         torch.cuda.synchronize(dev)
         ms64 = a0.elapsed_time(a1) / n64
         fp64 = {"value": npts / (ms64 * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms64, "steps": n64}
+        fpp = fp64_flops_per_point(g.nx, g.ny)
+        ach = fpp * npts / (ms64 * 1e-3) / 1e12
+        fp64["roofline"] = {"bound": "alu", "flops_per_point": fpp, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                            "peak_kind": "nominal FP64 FMA rate of a GB300", "unit": "TFLOP/s",
+                            "frac": ach / FP64_PEAK_TFLOPS}
         if not args.no_check and rank == 0:
             fp64["accuracy"] = verify(g, (u64, v64, w64), o64)
         P64.close()
