@@ -80,6 +80,19 @@ def test_grouped_batch_equals_individual_solves():
                 assert torch.equal(x, y)
 
     check()
+    # and every grouped instance against the FP64 oracle (inputs as the GPU saw them)
+    import oracle as O
+    for i, ((n, nz, prec), f) in enumerate(zip(spec, fields)):
+        g = W.make_grid(n, n, nz, 25.0, 25.0, W.geometric_dz(nz, 10.0, 100.0))
+        u, v, w = (t.double().cpu().numpy() for t in f[:3])
+        ref = O.project(u, v, w, g.dx, g.dy, g.dz, g.rho_c, g.rho_f)
+        got = [t.double().cpu().numpy() for t in f[3:6]]
+        num = sum(np.linalg.norm(a - b) ** 2 for a, b in zip(got, ref[:3]))
+        den = sum(np.linalg.norm(b) ** 2 for b in ref[:3])
+        tol = 1e-12 if prec == "fp64" else 1e-5
+        assert (num / den) ** 0.5 < tol, f"instance {i} ({n}x{n}x{nz} {prec})"
+        assert O.divergence_residual(*got, u, v, w, g.dx, g.dy, g.dz, g.rho_c, g.rho_f) < \
+            (1e-10 if prec == "fp64" else 1e-6)
     for f in fields:
         for t in f[3:]:
             if t is not None:
