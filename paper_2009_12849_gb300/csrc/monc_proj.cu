@@ -632,7 +632,13 @@ int setup_fused(monc_proj_plan_s* p) {
 // more blocks than fit would only wait for a slot).
 int setup_pipe(monc_proj_plan_s* p) {
     const KernelFn ff = pick_fwd_pipe(p->nx, p->ny, p->pipe_ef), fi = pick_inv_pipe(p->nx, p->ny, p->pipe_ef);
-    if (!ff || !fi || p->smem_pipe > kSmemMax || p->thr_cols != kPipeThreads) { p->pipe = false; return MONC_PROJ_OK; }
+    // the pipelines' column tasks have the padded pitch and the 256-thread tile
+    // width compiled in (PipeCols)
+    if (!ff || !fi || p->smem_pipe > kSmemMax || p->thr_cols != kPipeThreads ||
+        p->tw_cols * p->ny != kPipeThreads * kMaxRadixF32 || p->nxp != ((p->nxh + 15) & ~15)) {
+        p->pipe = false;
+        return MONC_PROJ_OK;
+    }
     int bf = 0, bi = 0;
     if (cudaFuncSetAttribute((const void*)ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_pipe) != cudaSuccess ||
         cudaFuncSetAttribute((const void*)fi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_pipe) != cudaSuccess ||

@@ -45,6 +45,14 @@ template <int NX> struct PipeRows {
     static constexpr int kRows = 2 * kPairs;
 };
 
+// Column tiles of the pipelines: the plan pads spectral rows to whole 128-byte
+// lines and the 256-thread tiles hold 256 * 32 / NY columns, so the pitch and
+// tile width are compile-time constants of (NX, NY).
+template <int NX, int NY> struct PipeCols {
+    static constexpr int NXP = ((NX / 2 + 1) + 15) & ~15;
+    static constexpr int TW = kPipeThreads * ElemsPerThread<float>::value / NY;
+};
+
 // The block waits until *ctr >= target (acquire by thread 0, then a barrier),
 // for at most `limit` polls after the first.
 __device__ __forceinline__ void pipe_wait(const unsigned* ctr, unsigned target, int* err, long long limit) {
@@ -142,7 +150,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2) k_fwd_pipe(ProjParams p) {
             pipe_signal(&done[k]);
         } else {
             pipe_wait(&done[k], (unsigned)a, p.err, p.spin_limit);
-            fwd_cols_task<float, NY>(p, smem_raw, k, idx);
+            fwd_cols_task<float, NY, PipeCols<NX, NY>::NXP, PipeCols<NX, NY>::TW>(p, smem_raw, k, idx);
         }
         t = tk.hand(&s_ticket);
     }
@@ -158,9 +166,10 @@ __global__ void __launch_bounds__(kPipeThreads, 2) k_inv_pipe(ProjParams p) {
     using RW = PipeRows<NX>;
     const int nz = p.nz;
     const int nch = p.nch;
-    const int nwt = ((p.ny + RW::kRows - 1) / RW::kRows) * nch;    // warp tasks per level
+    constexpr int BROWS = RW::kRows * kPipeWarps;                   // rows of a C task (the block's transforms)
+    const int nrb = (p.ny + BROWS - 1) / BROWS;
     const int a = 2 * p.ntiles;                                     // P tasks per level
-    const int b = (nwt + kPipeWarps - 1) / kPipeWarps;             // C block tasks per level
+    const int b = nrb * nch;                                        // C block tasks per level
     const int L = min(p.lag, nz);
     const int total = nz * (a + b);
     unsigned* done = p.sync + 2 + nz;
@@ -173,15 +182,12 @@ __global__ void __launch_bounds__(kPipeThreads, 2) k_inv_pipe(ProjParams p) {
         tk.take();
         int k, idx;
         if (pipe_decode(t, nz, L, a, b, &k, &idx)) {
-            inv_cols_tile<float, NY, false>(p, smem_raw, k, (idx >> 1) * p.tw_cols, idx & 1);
+            using PC = PipeCols<NX, NY>;
+            inv_cols_tile<float, NY, false, PC::NXP, PC::TW>(p, smem_raw, k, (idx >> 1) * PC::TW, idx & 1);
             pipe_signal(&done[k]);
         } else {
             pipe_wait(&done[k], (unsigned)a, p.err, p.spin_limit);
-            const int wt = idx * kPipeWarps + warp;
-            if (wt < nwt)
-                inv_rows_ct<float, NX, float, EF, WarpScope>(p, wslice, k, (wt / nch) * RW::kRows, wt % nch,
-                                                               RW::kRows);
-            __syncthreads();
+            inv_rows_ct<float, NX, float, EF, BlockScope>(p, smem_raw, k, (idx / nch) * BROWS, idx % nch, BROWS);
         }
         t = tk.hand(&s_ticket);
     }
