@@ -69,6 +69,11 @@ struct ProjParams {
     // vertical solve's spectral rows are ky_base .. ky_base + ny - 1.  A whole
     // solve has kbase = ky_base = 0 and nz_glob = nz.
     int kbase, nz_glob, ky_base;
+    // mixed plans: the 1/e of the FP64 warps' columns, [nz][nslots], and the
+    // first slot of each warp ([ny][nwr], -1 for FP32 warps); null otherwise
+    const double* gtab;
+    const int* wslot;
+    int nslots, nwr;
 };
 
 template <typename R> __device__ __forceinline__ const cplx<R>* ctab(const void* p) { return (const cplx<R>*)p; }
@@ -602,6 +607,99 @@ __device__ __forceinline__ void tridiag_column_mixed64(const ProjParams& p, size
     }
 }
 
+// 1/e of the FP64 warps' columns (one thread per column, plan time): the
+// forward sweep's pivots depend only on lambda and the vertical coefficients,
+// g_k = 1 / (lambda s_k - c_k - a_k^2 g_{k-1}), g_{-1} = 0, with the pinned
+// mean column's g_0 = 0.  wlist holds (ky, kx0) per warp.
+template <int D = 0>
+__global__ void __launch_bounds__(128) k_fp64_gtab(const int* __restrict__ wlist, const double* __restrict__ lamx,
+                                                   const double* __restrict__ lamy, const double* __restrict__ a,
+                                                   const double* __restrict__ sv, const double* __restrict__ cs,
+                                                   int nxh, int nz, int nslots, double* __restrict__ gtab) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nslots) return;
+    const int ky = wlist[2 * (t >> 5)], kx = wlist[2 * (t >> 5) + 1] + (t & 31);
+    if (kx >= nxh) {
+        for (int k = 0; k < nz; ++k) gtab[(size_t)k * nslots + t] = 0.0;
+        return;
+    }
+    const double lam = lamx[kx] + lamy[ky];
+    const bool mean = kx == 0 && ky == 0;
+    double g = 0.0;
+    for (int k = 0; k < nz; ++k) {
+        const double m = a[k] * g;
+        const double e = fma(-a[k], m, fma(lam, sv[k], -cs[k]));
+        g = (mean && k == 0) ? 0.0 : 1.0 / e;
+        gtab[(size_t)k * nslots + t] = g;
+    }
+}
+
+// FP64 column of a mixed plan with the plan's 1/e table: each level's
+// dependent work is the y update (and, going back, the p update); y.x in
+// S[k] and y.y in G[k] as doubles, as tridiag_column_mixed64.
+__device__ __forceinline__ void tridiag_column_tab64(const ProjParams& p, size_t base, int slot, bool mean) {
+    constexpr int B = kTriBatch64;
+    const int nz = p.nz;
+    const size_t LS = (size_t)p.ny * p.nxp;
+    float2* S = (float2*)p.S;
+    float2* G = (float2*)p.G;
+    double* Sd = (double*)p.S;
+    double* Gd = (double*)p.G;
+    const double* gt = p.gtab + slot;
+    const size_t GS = (size_t)p.nslots;
+    const double scale = p.scale;
+    double gp = 0.0;
+    double2 y = make_double2(0.0, 0.0);
+    for (int kb = 0; kb < nz; kb += B) {
+        float2 dv[B];
+        double gv[B];
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            const bool in = kb + i < nz;
+            dv[i] = in ? S[(kb + i) * LS + base] : make_float2(0.f, 0.f);
+            gv[i] = in ? gt[(kb + i) * GS] : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            const int k = kb + i;
+            if (k >= nz) break;
+            const size_t o = k * LS + base;
+            const double m = p.acoef[k] * gp;
+            double2 yk = make_double2((double)dv[i].x - m * y.x, (double)dv[i].y - m * y.y);
+            if (mean && k == 0) yk = make_double2(0.0, 0.0);
+            y = yk;
+            gp = gv[i];
+            Sd[o] = yk.x;
+            Gd[o] = yk.y;
+        }
+    }
+    double2 ph = make_double2(y.x * gp, y.y * gp);
+    S[(nz - 1) * LS + base] = make_float2((float)(ph.x * scale), (float)(ph.y * scale));
+    for (int kb = nz - 2; kb >= 0; kb -= B) {
+        double yx[B], yy[B], gv[B];
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            const int k = kb - i;
+            const size_t o = (k >= 0 ? k : 0) * LS + base;
+            yx[i] = (k >= 0) ? Sd[o] : 0.0;
+            yy[i] = (k >= 0) ? Gd[o] : 0.0;
+            gv[i] = (k >= 0) ? gt[(size_t)k * GS] : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            const int k = kb - i;
+            if (k < 0) break;
+            const size_t o = k * LS + base;
+            const double a1 = p.acoef[k + 1];
+            const double2 pn = make_double2((yx[i] - a1 * ph.x) * gv[i], (yy[i] - a1 * ph.y) * gv[i]);
+            const double iz = p.idzn[k + 1] * scale;
+            G[o + LS] = make_float2((float)((ph.x - pn.x) * iz), (float)((ph.y - pn.y) * iz));
+            S[o] = make_float2((float)(pn.x * scale), (float)(pn.y * scale));
+            ph = pn;
+        }
+    }
+}
+
 // FP32 column without a stored forward sweep: the forward sweep keeps only a
 // checkpoint (y, 1/e) at the start of every kTriSeg levels (thread-local
 // memory); the back substitution recomputes each segment's forward values in
@@ -712,7 +810,11 @@ __device__ __forceinline__ void tridiag_task(const ProjParams& p, long long col)
     } else {
         const double lam_warp = p.lamx[kx & ~31] + p.lamy[kyg];  // smallest |lambda| of the warp
         // the warp holding the mean column always runs FP64 (it carries the pin)
-        if (-lam_warp < p.lam_fp64 || (kyg == 0 && kx < 32)) tridiag_column_mixed64(p, base, lam, mean);
+        if (-lam_warp < p.lam_fp64 || (kyg == 0 && kx < 32)) {
+            const int ws = p.gtab ? p.wslot[kyg * p.nwr + (kx >> 5)] : -1;
+            if (ws >= 0) tridiag_column_tab64(p, base, ws + (kx & 31), mean);
+            else tridiag_column_mixed64(p, base, lam, mean);
+        }
         else if (p.nz <= kTriSeg * kTriMaxSeg) tridiag_column_ckpt32(p, base, (float)lam);
         else tridiag_column_inplace<float>(p, base, (float)lam, mean);
     }

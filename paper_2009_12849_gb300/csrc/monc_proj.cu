@@ -40,6 +40,12 @@ struct monc_proj_plan_s {
     const float* rflo32; const float* rfhi32;
     double lam_fp64;
     long long fp64_cols;
+    int nslots;                           // columns of the FP64 warps with a 1/e table (mixed plans)
+    int nwr;                              // warps per spectral row of the vertical solve
+    size_t gtab_bytes;                    // bytes of that table
+    const int* wlist;                     // device: (ky, kx0) of each FP64 warp
+    const int* wslot;                     // device: [ny][nwr] first slot of a warp, or -1
+    double* gtab;                         // device: [nz][nslots] 1/e
     const double* lamx; const double* lamy;
     const void* ex; const void* ey;
     int* err;
@@ -331,6 +337,7 @@ ProjParams make_params(const monc_proj_plan_s* p, const void* u, const void* v, 
     q.kbase = 0;
     q.nz_glob = p->nz;
     q.ky_base = 0;
+    q.gtab = p->gtab; q.wslot = p->wslot; q.nslots = p->nslots; q.nwr = p->nwr;
     q.rows_inv = p->rows_inv[q.nch == 4 ? 1 : 0];
     q.nrb_inv = (p->ny + q.rows_inv - 1) / q.rows_inv;
     return q;
@@ -691,6 +698,8 @@ int validate_grid(int nx, int ny, int nz, double dx, double dy, const double* dz
 // Offsets of the plan's device tables inside one contiguous blob.
 struct TableOffsets {
     size_t twx, twy, twy16, sv, rl, rh, a, iz, cs, sv32, a32, cs32, iz32, rl32, rh32, lx, ly, ex, ey, err;
+    size_t wlist, wslot;   // FP64 warps of a mixed plan: (ky, kx0) list and per-warp slot map
+    size_t gtab;           // 1/e table of their columns, filled on the device (past the uploaded blob)
 };
 
 // Fill the host-side part of a plan (sizes, radix plans, task shapes,
@@ -874,6 +883,39 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
     pad_blob(blob);
     to.err = blob.size();
     blob.resize(blob.size() + 256, 0);
+    // FP64 warps of a mixed plan (the near-zero wavenumbers and the warp of
+    // the pinned mean, the same rule as the vertical solve's): their 1/e
+    // depend on the column's lambda and the vertical coefficients only, so a
+    // table of them is built once per plan and the solve's FP64 chain per level
+    // shrinks to the y update
+    p->nslots = 0;
+    p->nwr = ((p->nxh + 31) & ~31) / 32;
+    p->gtab_bytes = 0;
+    to.wlist = to.wslot = to.gtab = 0;
+    if (precision == MONC_PROJ_MIXED && !z64) {
+        std::vector<int> wl, ws((size_t)ny * p->nwr, -1);
+        for (int ky = 0; ky < ny; ++ky)
+            for (int w = 0; w < p->nwr; ++w) {
+                const int kx0 = 32 * w;
+                if (-(lamx[kx0] + lamy[ky]) < p->lam_fp64 || (ky == 0 && w == 0)) {
+                    ws[(size_t)ky * p->nwr + w] = p->nslots;
+                    wl.push_back(ky);
+                    wl.push_back(kx0);
+                    p->nslots += 32;
+                }
+            }
+        auto push_ints = [&](const std::vector<int>& v) {
+            const size_t o = blob.size();
+            blob.resize(o + v.size() * sizeof(int));
+            std::memcpy(blob.data() + o, v.data(), v.size() * sizeof(int));
+            pad_blob(blob);
+            return o;
+        };
+        to.wlist = push_ints(wl);
+        to.wslot = push_ints(ws);
+        p->gtab_bytes = (size_t)p->nslots * nz * sizeof(double);
+        to.gtab = align256(blob.size());
+    }
 
     p->ct_rows = ctx;
     p->ct_cols = cty;
@@ -970,6 +1012,22 @@ void plan_bind(monc_proj_plan_s* p, unsigned char* db, const TableOffsets& to) {
     p->rflo32 = (const float*)(db + to.rl32); p->rfhi32 = (const float*)(db + to.rh32);
     p->lamy = (const double*)(db + to.ly); p->ex = db + to.ex; p->ey = db + to.ey;
     p->err = (int*)(db + to.err);
+    p->wlist = p->nslots ? (const int*)(db + to.wlist) : nullptr;
+    p->wslot = p->nslots ? (const int*)(db + to.wslot) : nullptr;
+    p->gtab = p->nslots ? (double*)(db + to.gtab) : nullptr;
+}
+
+// Device bytes of a plan's tables: the uploaded blob, then the 1/e table.
+size_t plan_table_bytes(const monc_proj_plan_s* p, size_t blob_bytes, const TableOffsets& to) {
+    return p->nslots ? to.gtab + p->gtab_bytes : blob_bytes;
+}
+
+// Fill the tables computed on the device (after the upload, on `st`).
+int plan_fill_tables(monc_proj_plan_s* p, cudaStream_t st) {
+    if (!p->nslots) return MONC_PROJ_OK;
+    k_fp64_gtab<<<(p->nslots + 127) / 128, 128, 0, st>>>(p->wlist, p->lamx, p->lamy, p->acoef, p->svol, p->csum,
+                                                          p->nxh, p->nz, p->nslots, p->gtab);
+    return cudaGetLastError() == cudaSuccess ? MONC_PROJ_OK : MONC_PROJ_ECUDA;
 }
 
 // Streams on which a batch's instances run concurrently (per device), with
@@ -1043,11 +1101,12 @@ int monc_proj_plan(monc_proj_plan_t* out, int nx, int ny, int nz, double dx, dou
     void* d = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_alloc_mu);
+        const size_t tb = plan_table_bytes(p, blob.size(), to);
         if (g_alloc) {
-            d = g_alloc(blob.size(), g_alloc_user);
+            d = g_alloc(tb, g_alloc_user);
             p->tables_free = g_free;
             p->tables_user = g_alloc_user;
-        } else if (cudaMalloc(&d, blob.size()) != cudaSuccess) {
+        } else if (cudaMalloc(&d, tb) != cudaSuccess) {
             cudaGetLastError();
             d = nullptr;
         }
@@ -1064,12 +1123,15 @@ int monc_proj_plan(monc_proj_plan_t* out, int nx, int ny, int nz, double dx, dou
     const int ar = plan_kernel_attrs(p);
     if (ar != MONC_PROJ_OK) return fail(ar);
     cudaStream_t st = (cudaStream_t)stream;
-    if (cudaMemcpyAsync(d, blob.data(), blob.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess) {
+    if (cudaMemcpyAsync(d, blob.data(), blob.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) {
         cudaGetLastError();
         return fail(MONC_PROJ_ECUDA);
     }
     plan_bind(p, (unsigned char*)d, to);
+    if (plan_fill_tables(p, st) != MONC_PROJ_OK || cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MONC_PROJ_ECUDA);
+    }
     *out = p;
     return MONC_PROJ_OK;
 }
@@ -1785,7 +1847,7 @@ extern "C" int monc_proj_solve_noalloc(int nx, int ny, int nz, double dx, double
     std::vector<unsigned char> blob;
     TableOffsets to{};
     plan_prepare(&plan, nx, ny, nz, dx, dy, dz, rho_c, rho_f, precision, blob, to);
-    const size_t tables = align256(blob.size());
+    const size_t tables = align256(plan_table_bytes(&plan, blob.size(), to));
     if (tables + plan.ws_bytes > (size_t)MONC_PROJ_NOALLOC_SCRATCH_BYTES) return MONC_PROJ_ESCRATCH;
     // the table upload reads `blob`, which dies with this call: a graph
     // captured here would replay a copy from freed host memory
@@ -1808,6 +1870,7 @@ extern "C" int monc_proj_solve_noalloc(int nx, int ny, int nz, double dx, double
     }
     unsigned char* b = (unsigned char*)base;
     plan_bind(&plan, b, to);
+    if (plan_fill_tables(&plan, st) != MONC_PROJ_OK) return MONC_PROJ_ECUDA;
     const ProjParams q = make_params(&plan, u, v, w, u_out, v_out, w_out, phi_out, b + tables);
     return run_solve(&plan, q, st);
 }
