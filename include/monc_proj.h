@@ -127,8 +127,12 @@ int monc_proj_set_allocator(monc_proj_alloc_fn alloc, monc_proj_free_fn release,
  *   rho_f      host array [nz+1], reference density at w faces, > 0
  *   precision  MONC_PROJ_FP64, MONC_PROJ_MIXED, MONC_PROJ_REFINED or
  *              MONC_PROJ_MIXED_Z64
- *   stream     cudaStream_t (may be NULL) used for the plan's uploads; the
- *              call returns after they have completed
+ *   stream     cudaStream_t (may be NULL) used for the plan's uploads and, in
+ *              mixed plans, the kernel that fills the table of the FP64
+ *              columns' pivots (1/e of the vertical elimination, which depend
+ *              on lambda and the vertical coefficients only: 8 bytes per level
+ *              and column of the near-zero-wavenumber warps); the call returns
+ *              after they have completed
  *
  * The host arrays are copied; the caller may free them when this returns.
  * The plan's device tables live on the device that is current at the call.
@@ -382,7 +386,8 @@ int monc_proj_unpack_pencils(monc_proj_plan_t plan, int nzl, int parts, const vo
  *    64 x 64 x 64 in FP64 or 80 x 80 x 64 in mixed precision fit);
  *  - every call looks up the array's device address on the current device
  *    (cudaGetSymbolAddress), so nothing is cached across calls or contexts;
- *  - the tables are uploaded at every call with cudaMemcpyAsync from pageable
+ *  - the tables are uploaded (and a mixed plan's FP64 pivot table filled by a
+ *    kernel) at every call; the upload is a cudaMemcpyAsync from pageable
  *    host memory that the call owns only while it runs, so the call may wait
  *    for the work already on `stream` before it returns, and a call on a
  *    stream that is being captured into a CUDA graph is refused with
