@@ -69,9 +69,11 @@ struct ProjParams {
     // vertical solve's spectral rows are ky_base .. ky_base + ny - 1.  A whole
     // solve has kbase = ky_base = 0 and nz_glob = nz.
     int kbase, nz_glob, ky_base;
-    // mixed plans: the 1/e of the FP64 warps' columns, [nz][nslots], and the
-    // first slot of each warp ([ny][nwr], -1 for FP32 warps); null otherwise
-    const double* gtab;
+    // mixed plans: the pivots of the FP64 warps' columns as FP32 pairs,
+    // [nz][nslots] each: pvm = a_k / e_{k-1}, pvgb = (1/e_k, a_{k+1} / e_k);
+    // and the first slot of each warp ([ny][nwr], -1 for FP32 warps); null otherwise
+    const float2* pvm;
+    const float4* pvgb;
     const int* wslot;
     int nslots, nwr;
 };
@@ -607,95 +609,131 @@ __device__ __forceinline__ void tridiag_column_mixed64(const ProjParams& p, size
     }
 }
 
-// 1/e of the FP64 warps' columns (one thread per column, plan time): the
-// forward sweep's pivots depend only on lambda and the vertical coefficients,
-// g_k = 1 / (lambda s_k - c_k - a_k^2 g_{k-1}), g_{-1} = 0, with the pinned
-// mean column's g_0 = 0.  wlist holds (ky, kx0) per warp.
+// Arithmetic on FP32 pairs (hi + lo, |lo| <= ulp(hi)/2; Dekker's and Knuth's
+// error-free transformations, the product through a fused multiply-add): about
+// 48 bits of precision on the FP32 pipes, which GB300 runs 64 times faster than
+// its FP64 pipe.
+struct F2P {
+    float hi, lo;
+};
+__device__ __forceinline__ F2P fp_fast_two_sum(float a, float b) {     // |a| >= |b|
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ F2P fp_two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ F2P fp_mul(F2P a, F2P b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    return fp_fast_two_sum(p, e);
+}
+__device__ __forceinline__ F2P fp_sub(F2P a, F2P b) {
+    const F2P s = fp_two_sum(a.hi, -b.hi);
+    return fp_fast_two_sum(s.hi, s.lo + (a.lo - b.lo));
+}
+
+// Pivots of the FP64 warps' columns (one thread per column, plan time): the
+// forward sweep's 1/e_k = 1 / (lambda s_k - c_k - a_k^2 / e_{k-1}) depend
+// only on lambda and the vertical coefficients (1/e_{-1} = 0; the pinned mean
+// column has 1/e_0 = 0).  Computed in FP64 and stored as FP32 pairs: pvm[k] =
+// a_k / e_{k-1}, pvgb[k] = (1/e_k, a_{k+1} / e_k).  wlist holds (ky, kx0) per warp.
+__device__ __forceinline__ float2 split_pair(double x) {
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+}
 template <int D = 0>
-__global__ void __launch_bounds__(128) k_fp64_gtab(const int* __restrict__ wlist, const double* __restrict__ lamx,
-                                                   const double* __restrict__ lamy, const double* __restrict__ a,
-                                                   const double* __restrict__ sv, const double* __restrict__ cs,
-                                                   int nxh, int nz, int nslots, double* __restrict__ gtab) {
+__global__ void __launch_bounds__(128) k_fp64_pivots(const int* __restrict__ wlist, const double* __restrict__ lamx,
+                                                     const double* __restrict__ lamy, const double* __restrict__ a,
+                                                     const double* __restrict__ sv, const double* __restrict__ cs,
+                                                     int nxh, int nz, int nslots, float2* __restrict__ pvm,
+                                                     float4* __restrict__ pvgb) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nslots) return;
     const int ky = wlist[2 * (t >> 5)], kx = wlist[2 * (t >> 5) + 1] + (t & 31);
-    if (kx >= nxh) {
-        for (int k = 0; k < nz; ++k) gtab[(size_t)k * nslots + t] = 0.0;
-        return;
-    }
-    const double lam = lamx[kx] + lamy[ky];
+    const double lam = kx < nxh ? lamx[kx] + lamy[ky] : -1.0;
     const bool mean = kx == 0 && ky == 0;
     double g = 0.0;
     for (int k = 0; k < nz; ++k) {
         const double m = a[k] * g;
         const double e = fma(-a[k], m, fma(lam, sv[k], -cs[k]));
         g = (mean && k == 0) ? 0.0 : 1.0 / e;
-        gtab[(size_t)k * nslots + t] = g;
+        const double b = (k + 1 < nz ? a[k + 1] : 0.0) * g;
+        const size_t o = (size_t)k * nslots + t;
+        pvm[o] = split_pair(m);
+        const float2 gh = split_pair(g), bh = split_pair(b);
+        pvgb[o] = make_float4(gh.x, gh.y, bh.x, bh.y);
     }
 }
 
-// FP64 column of a mixed plan with the plan's 1/e table: each level's
-// dependent work is the y update (and, going back, the p update); y.x in
-// S[k] and y.y in G[k] as doubles, as tridiag_column_mixed64.
-__device__ __forceinline__ void tridiag_column_tab64(const ProjParams& p, size_t base, int slot, bool mean) {
-    constexpr int B = kTriBatch64;
+// FP64-class column of a mixed plan on FP32 pairs with the plan's pivots:
+// forward y_k = D'_k - (a_k/e_{k-1}) y_{k-1}, back p_k = y_k/e_k - (a_{k+1}/e_k)
+// p_{k+1}, everything in FP32-pair arithmetic; y is kept between the sweeps
+// as pairs (real part in S[k], imaginary part in G[k]).
+__device__ __forceinline__ void tridiag_column_pair(const ProjParams& p, size_t base, int slot, bool mean) {
+    constexpr int B = 4;                    // levels per batch of loads (registers)
     const int nz = p.nz;
     const size_t LS = (size_t)p.ny * p.nxp;
     float2* S = (float2*)p.S;
     float2* G = (float2*)p.G;
-    double* Sd = (double*)p.S;
-    double* Gd = (double*)p.G;
-    const double* gt = p.gtab + slot;
+    const float2* pm = p.pvm + slot;
+    const float4* pg = p.pvgb + slot;
     const size_t GS = (size_t)p.nslots;
-    const double scale = p.scale;
-    double gp = 0.0;
-    double2 y = make_double2(0.0, 0.0);
+    const float scale = (float)p.scale;
+    F2P yr{0.f, 0.f}, yi{0.f, 0.f};
     for (int kb = 0; kb < nz; kb += B) {
-        float2 dv[B];
-        double gv[B];
+        float2 dv[B], mv[B];
 #pragma unroll
         for (int i = 0; i < B; ++i) {
             const bool in = kb + i < nz;
             dv[i] = in ? S[(kb + i) * LS + base] : make_float2(0.f, 0.f);
-            gv[i] = in ? gt[(kb + i) * GS] : 0.0;
+            mv[i] = in ? pm[(kb + i) * GS] : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int i = 0; i < B; ++i) {
             const int k = kb + i;
             if (k >= nz) break;
+            const F2P m{mv[i].x, mv[i].y};
+            yr = fp_sub(F2P{dv[i].x, 0.f}, fp_mul(m, yr));
+            yi = fp_sub(F2P{dv[i].y, 0.f}, fp_mul(m, yi));
+            if (mean && k == 0) yr = yi = F2P{0.f, 0.f};
             const size_t o = k * LS + base;
-            const double m = p.acoef[k] * gp;
-            double2 yk = make_double2((double)dv[i].x - m * y.x, (double)dv[i].y - m * y.y);
-            if (mean && k == 0) yk = make_double2(0.0, 0.0);
-            y = yk;
-            gp = gv[i];
-            Sd[o] = yk.x;
-            Gd[o] = yk.y;
+            S[o] = make_float2(yr.hi, yr.lo);
+            G[o] = make_float2(yi.hi, yi.lo);
         }
     }
-    double2 ph = make_double2(y.x * gp, y.y * gp);
-    S[(nz - 1) * LS + base] = make_float2((float)(ph.x * scale), (float)(ph.y * scale));
+    // top level: p = y / e
+    const float4 gt = pg[(size_t)(nz - 1) * GS];
+    F2P pr = fp_mul(yr, F2P{gt.x, gt.y}), pi = fp_mul(yi, F2P{gt.x, gt.y});
+    S[(nz - 1) * LS + base] = make_float2(pr.hi * scale, pi.hi * scale);
     for (int kb = nz - 2; kb >= 0; kb -= B) {
-        double yx[B], yy[B], gv[B];
+        float2 ys[B], yg[B];
+        float4 gv[B];
 #pragma unroll
         for (int i = 0; i < B; ++i) {
             const int k = kb - i;
             const size_t o = (k >= 0 ? k : 0) * LS + base;
-            yx[i] = (k >= 0) ? Sd[o] : 0.0;
-            yy[i] = (k >= 0) ? Gd[o] : 0.0;
-            gv[i] = (k >= 0) ? gt[(size_t)k * GS] : 0.0;
+            ys[i] = (k >= 0) ? S[o] : make_float2(0.f, 0.f);
+            yg[i] = (k >= 0) ? G[o] : make_float2(0.f, 0.f);
+            gv[i] = (k >= 0) ? pg[(size_t)k * GS] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int i = 0; i < B; ++i) {
             const int k = kb - i;
             if (k < 0) break;
             const size_t o = k * LS + base;
-            const double a1 = p.acoef[k + 1];
-            const double2 pn = make_double2((yx[i] - a1 * ph.x) * gv[i], (yy[i] - a1 * ph.y) * gv[i]);
-            const double iz = p.idzn[k + 1] * scale;
-            G[o + LS] = make_float2((float)((ph.x - pn.x) * iz), (float)((ph.y - pn.y) * iz));
-            S[o] = make_float2((float)(pn.x * scale), (float)(pn.y * scale));
-            ph = pn;
+            const F2P g{gv[i].x, gv[i].y}, b{gv[i].z, gv[i].w};
+            const F2P nr = fp_sub(fp_mul(F2P{ys[i].x, ys[i].y}, g), fp_mul(b, pr));
+            const F2P ni = fp_sub(fp_mul(F2P{yg[i].x, yg[i].y}, g), fp_mul(b, pi));
+            const float iz = (float)p.idzn[k + 1] * scale;
+            const F2P dr = fp_sub(pr, nr), di = fp_sub(pi, ni);
+            G[o + LS] = make_float2((dr.hi + dr.lo) * iz, (di.hi + di.lo) * iz);
+            S[o] = make_float2(nr.hi * scale, ni.hi * scale);
+            pr = nr;
+            pi = ni;
         }
     }
 }
@@ -811,8 +849,8 @@ __device__ __forceinline__ void tridiag_task(const ProjParams& p, long long col)
         const double lam_warp = p.lamx[kx & ~31] + p.lamy[kyg];  // smallest |lambda| of the warp
         // the warp holding the mean column always runs FP64 (it carries the pin)
         if (-lam_warp < p.lam_fp64 || (kyg == 0 && kx < 32)) {
-            const int ws = p.gtab ? p.wslot[kyg * p.nwr + (kx >> 5)] : -1;
-            if (ws >= 0) tridiag_column_tab64(p, base, ws + (kx & 31), mean);
+            const int ws = p.pvm ? p.wslot[kyg * p.nwr + (kx >> 5)] : -1;
+            if (ws >= 0) tridiag_column_pair(p, base, ws + (kx & 31), mean);
             else tridiag_column_mixed64(p, base, lam, mean);
         }
         else if (p.nz <= kTriSeg * kTriMaxSeg) tridiag_column_ckpt32(p, base, (float)lam);

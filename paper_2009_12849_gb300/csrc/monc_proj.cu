@@ -45,7 +45,8 @@ struct monc_proj_plan_s {
     size_t gtab_bytes;                    // bytes of that table
     const int* wlist;                     // device: (ky, kx0) of each FP64 warp
     const int* wslot;                     // device: [ny][nwr] first slot of a warp, or -1
-    double* gtab;                         // device: [nz][nslots] 1/e
+    float2* pvm;                          // device: [nz][nslots] a_k / e_{k-1} (FP32 pair)
+    float4* pvgb;                         // device: [nz][nslots] (1/e_k, a_{k+1} / e_k) (FP32 pairs)
     const double* lamx; const double* lamy;
     const void* ex; const void* ey;
     int* err;
@@ -337,7 +338,7 @@ ProjParams make_params(const monc_proj_plan_s* p, const void* u, const void* v, 
     q.kbase = 0;
     q.nz_glob = p->nz;
     q.ky_base = 0;
-    q.gtab = p->gtab; q.wslot = p->wslot; q.nslots = p->nslots; q.nwr = p->nwr;
+    q.pvm = p->pvm; q.pvgb = p->pvgb; q.wslot = p->wslot; q.nslots = p->nslots; q.nwr = p->nwr;
     q.rows_inv = p->rows_inv[q.nch == 4 ? 1 : 0];
     q.nrb_inv = (p->ny + q.rows_inv - 1) / q.rows_inv;
     return q;
@@ -913,7 +914,7 @@ void plan_prepare(monc_proj_plan_s* p, int nx, int ny, int nz, double dx, double
         };
         to.wlist = push_ints(wl);
         to.wslot = push_ints(ws);
-        p->gtab_bytes = (size_t)p->nslots * nz * sizeof(double);
+        p->gtab_bytes = (size_t)p->nslots * nz * (sizeof(float2) + sizeof(float4));
         to.gtab = align256(blob.size());
     }
 
@@ -1014,7 +1015,8 @@ void plan_bind(monc_proj_plan_s* p, unsigned char* db, const TableOffsets& to) {
     p->err = (int*)(db + to.err);
     p->wlist = p->nslots ? (const int*)(db + to.wlist) : nullptr;
     p->wslot = p->nslots ? (const int*)(db + to.wslot) : nullptr;
-    p->gtab = p->nslots ? (double*)(db + to.gtab) : nullptr;
+    p->pvm = p->nslots ? (float2*)(db + to.gtab) : nullptr;
+    p->pvgb = p->nslots ? (float4*)(db + to.gtab + (size_t)p->nslots * p->nz * sizeof(float2)) : nullptr;
 }
 
 // Device bytes of a plan's tables: the uploaded blob, then the 1/e table.
@@ -1025,8 +1027,8 @@ size_t plan_table_bytes(const monc_proj_plan_s* p, size_t blob_bytes, const Tabl
 // Fill the tables computed on the device (after the upload, on `st`).
 int plan_fill_tables(monc_proj_plan_s* p, cudaStream_t st) {
     if (!p->nslots) return MONC_PROJ_OK;
-    k_fp64_gtab<<<(p->nslots + 127) / 128, 128, 0, st>>>(p->wlist, p->lamx, p->lamy, p->acoef, p->svol, p->csum,
-                                                          p->nxh, p->nz, p->nslots, p->gtab);
+    k_fp64_pivots<<<(p->nslots + 127) / 128, 128, 0, st>>>(p->wlist, p->lamx, p->lamy, p->acoef, p->svol,
+                                                            p->csum, p->nxh, p->nz, p->nslots, p->pvm, p->pvgb);
     return cudaGetLastError() == cudaSuccess ? MONC_PROJ_OK : MONC_PROJ_ECUDA;
 }
 
