@@ -464,9 +464,11 @@ def main():
 
     # ---- the vertical solve with FP64 elimination on every column (FP32
     # storage): the reading of a3 in which no column runs FP32 arithmetic
-    a3_variants = {"fp32_fp64_split": {"ms_per_step": ms, "value": value, "unit": UNIT,
-                                       "fp64_columns": P.info().get("fp64_columns"),
-                                       "columns": P.info().get("total_columns")}}
+    # (the default: FP32 elimination, near-zero-wavenumber columns in FP32-pair
+    # arithmetic with FP64 pivots from the plan)
+    a3_variants = {"fp32_with_pair_near_zero": {"ms_per_step": ms, "value": value, "unit": UNIT,
+                                                "near_zero_columns": P.info().get("fp64_columns"),
+                                                "columns": P.info().get("total_columns")}}
     if not args.no_fp64:
         PZ = MP.Projector.from_grid(g, "mixed_z64", dev)
         oz = (torch.empty_like(u), torch.empty_like(v), torch.empty_like(w))
