@@ -4,9 +4,9 @@ batch (solved as one batch) and a sample of 20 served requests (solved by the
 serving loop), each at <= 1e-5 relative error and <= 1e-6 divergence
 residual; the full-size 1024^2 x 256 case is tests/test_z_fullsize.py.
 
-Both readings of the vertical solve run: MONC_PROJ_MIXED (FP64 elimination for
-the near-zero wavenumbers, FP32 for the rest) and MONC_PROJ_MIXED_Z64 (FP64
-elimination on every column).  Small grids are checked against the full
+Both readings of the vertical solve run: MONC_PROJ_MIXED (FP32-pair
+elimination with FP64 pivots for the near-zero wavenumbers, FP32 for the rest)
+and MONC_PROJ_MIXED_Z64 (FP64 elimination on every column).  Small grids are checked against the full
 oracle element by element, the others at sampled modes (the oracle solves
 each (kx, ky) alone) plus the residual over every cell.  Inputs are FP32
 draws that both sides read.
@@ -136,3 +136,29 @@ def test_served_requests_against_oracle():
         worst = (max(worst[0], err), max(worst[1], div))
     print(f"{len(reqs)} served requests: worst rel err {worst[0]:.2e}, worst divergence residual {worst[1]:.2e}")
     srv.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "mixed_z64"])
+def test_ill_conditioned_columns(prec):
+    """A grid whose columns are badly conditioned: wide cells (dx = dy = 200 m,
+    so |lambda| <= 2e-4 against a vertical operator bound near 1), 256 levels
+    from 2 m at the ground to 100 m at the top (kappa up to ~2e6).  Every
+    column falls below the near-zero threshold and takes the FP32-pair path;
+    against the full FP64 oracle at the mixed tolerances."""
+    mp = _mp()
+    nz = 256
+    g = W.make_grid(48, 40, nz, 200.0, 200.0, W.geometric_dz(nz, 2.0, 100.0))
+    ins = f32(W.random_fields(g, 31, True))
+    dev = torch.device("cuda", 0)
+    P = mp.Projector.from_grid(g, prec, dev)
+    info = P.info()
+    out = P.solve(*(torch.from_numpy(a).to(dev) for a in ins))
+    torch.cuda.synchronize()
+    assert P.sync_status() == 0
+    err, div = check(g, ins, [o.cpu().numpy() for o in out], full_oracle=True)
+    print(f"ill-conditioned {prec}: {info['fp64_columns']} of {info['total_columns']} near-zero columns, "
+          f"rel err {err:.2e}, divergence residual {div:.2e}")
+    if prec == "mixed":
+        assert info["fp64_columns"] > info["total_columns"] // 4
+    assert err <= ERR and div <= DIV
+    P.close()
