@@ -124,8 +124,11 @@ class ProjectionServer:
         kernel the stream will use before the first arrival (it loads a
         kernel on its first launch, a few ms each); and grow the allocator's
         pool to the HBM budget once (request buffers are carved from it, so
-        the serving loop makes no device allocation).  Returns the set-up
-        time [s]."""
+        the serving loop makes no device allocation).  The serving loop's
+        own first-use work is done here too: one request's fields generated
+        and one solve run on every slot stream with an event recorded (the
+        field generator's kernels load on their first launch as well).
+        Returns the set-up time [s]."""
         t = time.perf_counter()
         for n, nz in sizes:
             self.plans.get(n, nz, self.precision)
@@ -139,6 +142,20 @@ class ProjectionServer:
             w = torch.zeros((nz + 1, n, n), dtype=self.dtype, device=self.device)
             ws = torch.empty(max(plan.workspace_bytes, 256), dtype=torch.uint8, device=self.device)
             MP.monc_proj_solve(plan.handle, u, v, w, u, v, w, None, ws, torch.cuda.current_stream(self.device))
+            del u, v, w, ws
+        if smallest:
+            n, nz = min(smallest.items())
+            plan = self.plans.get(n, nz, self.precision)
+            u = torch.empty((nz, n, n), dtype=self.dtype, device=self.device)
+            v = torch.empty_like(u)
+            w = torch.empty((nz + 1, n, n), dtype=self.dtype, device=self.device)
+            ws = torch.empty(max(plan.workspace_bytes, 256), dtype=torch.uint8, device=self.device)
+            for stream in self.streams:
+                with torch.cuda.stream(stream):
+                    make_fields(Request(0.0, n, nz, 0), self.dtype, self.device, self.generator, out=(u, v, w))
+                    MP.monc_proj_solve(plan.handle, u, v, w, u, v, w, None, ws, stream)
+                    torch.cuda.Event(enable_timing=True).record(stream)
+                stream.synchronize()
             del u, v, w, ws
         free, _ = torch.cuda.mem_get_info(self.device)
         pool = int(min(self.hbm_budget, 0.8 * free))
