@@ -41,15 +41,25 @@ __global__ void __launch_bounds__(512) k_fwd_rows_grp(const __grid_constant__ Gr
                                                        p.rows_fwd);
 }
 
-// a2 (y): block = (level, tile)
-template <int NY>
+// Spectral pitch and tile width of an n x n FP32 plan with the default
+// 256-thread column tiles (the plan's set_task_shapes), for the column kernels
+// that take them at compile time.
+template <int N> struct GroupCols {
+    static constexpr int NXP = ((N / 2 + 1) + 3) & ~3;
+    static constexpr int TW0 = 256 * 32 / N < 32 ? 256 * 32 / N : 32;
+    static constexpr int TW = TW0 < N / 2 + 1 ? TW0 : N / 2 + 1;
+};
+
+// a2 (y): block = (level, tile); SQ: square grid with GroupCols' pitch and tile
+template <int NY, bool SQ = false>
 __global__ void __launch_bounds__(512) k_fwd_cols_grp(const __grid_constant__ GroupArgs g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int i = group_instance(g, blockIdx.x);
     const ProjParams& p = g.p[i];
     const int b = blockIdx.x - g.start[i];
     const int k = b / p.ntiles;
-    fwd_cols_task<float, NY>(p, smem_raw, k, b - k * p.ntiles);
+    if constexpr (SQ) fwd_cols_task<float, NY, GroupCols<NY>::NXP, GroupCols<NY>::TW>(p, smem_raw, k, b - k * p.ntiles);
+    else fwd_cols_task<float, NY>(p, smem_raw, k, b - k * p.ntiles);
 }
 
 // a3: kTriThreads columns per block (any horizontal size)
@@ -60,7 +70,7 @@ __global__ void __launch_bounds__(kTriThreads, 1024 / kTriThreads) k_tridiag_grp
 }
 
 // a4 (y): block = (level, tile, kind)
-template <int NY>
+template <int NY, bool SQ = false>
 __global__ void __launch_bounds__(512) k_inv_cols_grp(const __grid_constant__ GroupArgs g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int i = group_instance(g, blockIdx.x);
@@ -68,7 +78,11 @@ __global__ void __launch_bounds__(512) k_inv_cols_grp(const __grid_constant__ Gr
     const int b = blockIdx.x - g.start[i];
     const int task = b >> 1;
     const int k = task / p.ntiles;
-    inv_cols_tile<float, NY, false>(p, smem_raw, k, (task - k * p.ntiles) * p.tw_cols, b & 1);
+    using GC = GroupCols<NY>;
+    if constexpr (SQ)
+        inv_cols_tile<float, NY, false, GC::NXP, GC::TW>(p, smem_raw, k, (task - k * p.ntiles) * GC::TW, b & 1);
+    else
+        inv_cols_tile<float, NY, false>(p, smem_raw, k, (task - k * p.ntiles) * p.tw_cols, b & 1);
 }
 
 // a4 (x) + a5: block = (level, row block, channel)

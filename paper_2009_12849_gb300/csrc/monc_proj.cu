@@ -1525,7 +1525,8 @@ int launch_group_chunk(const monc_proj_plan_t* plans, const monc_proj_fields* fi
             case 3: thr = p0->thr_cols; smem = p0->smem_cols; break;
             default: thr = p0->thr_inv_rows[inv_idx]; smem = p0->smem_inv_rows[inv_idx]; break;
         }
-        const GroupFn fn = pick_group_f32(phase, (phase == 0 || phase == 4) ? p0->nx : p0->ny);
+        const GroupFn fn = pick_group_f32(phase, (phase == 0 || phase == 4) ? p0->nx : p0->ny, p0->nx == p0->ny,
+                                          p0->nxp, p0->tw_cols);
         if (!fn) return MONC_PROJ_EUNSUPPORTED;
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=

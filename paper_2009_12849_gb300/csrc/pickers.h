@@ -32,7 +32,9 @@ KernelFn pick_cols_square_f32(int ny, int nxp, int tw, int bs, bool inv, int e);
 // nullptr when n has no compile-time plan
 struct GroupArgs;
 using GroupFn = void (*)(const GroupArgs);
-GroupFn pick_group_f32(int phase, int n);
+// (square: nx = ny; with nxp and tw the group's spectral pitch and tile width,
+// which select the column kernels that have them compiled in when they match)
+GroupFn pick_group_f32(int phase, int n, bool square = false, int nxp = 0, int tw = 0);
 // FP32 persistent pipelines of the forward and inverse transforms (pipe.cuh);
 // nullptr for grids without them
 // (ef: the variants streaming u, v, w with evict-first L2 priority)
