@@ -23,6 +23,10 @@ KernelFn pick_cols_square_f32(int ny, int nxp, int tw, int bs, bool inv, int e) 
     MP_SQ(1024, 516, 8, 32)
     MP_SQ(512, 260, 16, 32)
     MP_SQ(256, 132, 32, 32)
+    MP_SQ(192, 100, 32, 32)
+    MP_SQ(128, 68, 32, 32)
+    MP_SQ(96, 52, 32, 32)
+    MP_SQ(64, 36, 32, 32)
     // the E = 16 schedule with 256-thread tiles
     MP_SQ(1024, 516, 4, 16)
     MP_SQ(512, 260, 8, 16)

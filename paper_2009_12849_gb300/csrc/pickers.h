@@ -23,8 +23,9 @@ template <typename R> KernelFn pick_fwd_fused(int n);
 template <typename R> KernelFn pick_inv_fused(int n);
 template <typename R> KernelFn pick_tridiag();
 // FP32 column kernels with the spectral pitch, tile width and radix schedule
-// (e: elements per thread, 32 or 16) fixed at compile time (nx = ny = 256,
-// 512, 1024 with 256-thread tiles); nullptr otherwise
+// (e: elements per thread, 32 or 16) fixed at compile time (nx = ny = 64, 96,
+// 128, 192, 256, 512, 1024 with the default tiles; E = 16 for 256, 512, 1024
+// with 256-thread tiles); nullptr otherwise
 KernelFn pick_cols_square_f32(int ny, int nxp, int tw, int bs, bool inv, int e);
 // grouped-launch kernels of batched FP32 projections (group.cuh): phase 0..4
 // = forward rows, forward columns, vertical solve, inverse columns, inverse
